@@ -1,0 +1,442 @@
+#!/usr/bin/env python3
+"""Throughput of VGICP factor linearization on one GB300 per rank.
+
+Workload (default): the global-map factor set of arXiv 2202.00242 Sec. III-F
+(a matching-cost factor for every overlapping submap pair) on a seeded
+synthetic city loop: 500 submaps with log-uniform 30k-80k points each, 5,000
+factor pairs (each submap is the source of factors to its 10 nearest submaps),
+pose perturbation 0.1 m / 1 deg, voxel resolution 1.0 m.
+
+One step = one pass of the whole hot path: (re)build the 500 target voxel maps
+(Sec. III-A voxelization) and linearize all 5,000 factors (Eqs. 2-3 -> H, b, err)
+in one batched launch.  Metric: source points per second (sum over the
+factors of their source cloud sizes / step time).  Inputs (0.9 GB of points and
+covariances) are larger than the 129 MB L2, so no explicit flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VGICP linearize: source pts/s and % HBM peak; batched vs per-factor"
+BYTES_PER_POINT = 36  # xyz (12 B) + 6-float covariance (24 B) per source point per factor
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--submaps", type=int, default=500)
+    ap.add_argument("--neighbours-per-submap", type=int, default=10)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU time budget of the oracle baseline sample")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--seed", type=int, default=3)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# ranks
+# ---------------------------------------------------------------------------
+
+def rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    rank, world, _ = rank_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Max of a float over all ranks (the step time of the slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device="cpu") -> float:
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(args, rank):
+    from paper_2202_00242_gb300 import synth
+    w = synth.config_global_map(seed=args.seed + 1000 * rank, n_submaps=args.submaps,
+                                neighbours=args.neighbours_per_submap)
+    return synth.with_surface_covariances(w)
+
+
+def workload_config(w, args, extra=None):
+    sizes = w.clouds.sizes
+    cfg = {
+        "workload": f"global_map_{len(sizes)}submaps_{w.pairs.shape[0]}pairs_r{w.resolution:g}",
+        "submaps": int(len(sizes)),
+        "pairs": int(w.pairs.shape[0]),
+        "points_per_submap": [int(sizes.min()), int(sizes.max())],
+        "target_points": int(sizes.sum()),
+        "source_points_per_step": int(w.source_points_per_step),
+        "resolution_m": w.resolution,
+        "neighbours": 1,
+        "step": "rebuild all target voxel maps + batched linearization of all pairs",
+        "covariances": "surface-normal Gaussians, eigenvalues (1, 1, 1e-3)",
+        "l2": f"inputs larger than L2 ({w.clouds.points.nbytes * 3 / 1e9:.2f} GB of points+covs)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch):
+    try:
+        return str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, budget_s, nthreads, start_pair=0, min_pairs=2):
+    """Build the needed target maps and linearize pairs in order until the
+    budget is spent.  Returns (source points, seconds, pairs done)."""
+    import oracle
+    oracle.build()
+    pts_done = 0
+    t0 = time.perf_counter()
+    maps = {}
+    p = start_pair
+    done = 0
+    while True:
+        j, i = (int(x) for x in w.pairs[p % w.pairs.shape[0]])
+        if j not in maps:
+            tp, tc = w.clouds.cloud(j)
+            maps[j] = oracle.build_voxelmap(tp, tc, w.resolution)
+        sp, sc = w.clouds.cloud(i)
+        oracle.linearize(maps[j], sp, sc, w.poses[p % w.pairs.shape[0]], nthreads=nthreads)
+        pts_done += sp.shape[0]
+        p += 1
+        done += 1
+        if done >= min_pairs and time.perf_counter() - t0 >= budget_s:
+            break
+    return pts_done, time.perf_counter() - t0, done
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    init_dist("nccl")
+    from paper_2202_00242_gb300 import _lib, api, build
+    build.build()
+    lib = _lib.load()
+    dev = torch.device("cuda", local)
+
+    w = make_workload(args, rank)
+    off = w.clouds.offsets
+    C = len(off) - 1
+    pts = torch.from_numpy(w.clouds.points).to(dev)
+    covs = torch.from_numpy(w.clouds.covs).to(dev)
+    maps = api.build_voxelmaps(pts, covs, off, w.resolution)
+    maps[0].status()
+    srcs = [(pts[off[c]:off[c + 1]], covs[off[c]:off[c + 1]]) for c in range(C)]
+    P = w.pairs.shape[0]
+    out = torch.empty((P, api.RESULT_SIZE), dtype=torch.float64, device=dev)
+    inl = torch.empty(P, dtype=torch.int64, device=dev)
+    n_pts = w.source_points_per_step
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        api.rebuild_voxelmaps(maps, pts, covs)
+        kw = {}
+        if ev is not None:
+            kw = {"events": ev}
+        linearize_batched_timed(api, maps, srcs, w.pairs, w.poses, out, inl, args, **kw)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    for m in maps:
+        m.status()
+
+    K = args.steps
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    for a, b in kev:  # create the underlying events before the library records them
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_uuid(torch))
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.vgicp_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(K):
+        step(kev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = lib.vgicp_launch_count() - launches0
+    clk = clocks.stop()
+    ms_local = t_start.elapsed_time(t_end) / K
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    ms = max_over_ranks(ms_local, world, dev)
+    total_pts = sum_over_ranks(n_pts, world, dev)
+    value = total_pts / (ms / 1e3)
+
+    # e2e through the public API: pinned host clouds in, results out, every step
+    pts_h = torch.from_numpy(w.clouds.points).pin_memory()
+    covs_h = torch.from_numpy(w.clouds.covs).pin_memory()
+    out_h = torch.empty_like(out, device="cpu").pin_memory()
+    inl_h = torch.empty_like(inl, device="cpu").pin_memory()
+    E = max(args.e2e_steps, 2)
+
+    def e2e_step():
+        pts.copy_(pts_h, non_blocking=True)
+        covs.copy_(covs_h, non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
+        inl_h.copy_(inl, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(E):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / E, world, dev)
+    e2e_value = total_pts / (e2e_ms / 1e3)
+    h2d = pts_h.numel() * 4 + covs_h.numel() * 4
+    d2h = out_h.numel() * 8 + inl_h.numel() * 8
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = BYTES_PER_POINT * n_pts / (kernel_ms / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        n_done, secs, pairs_done = oracle_sample(w, args.cpu_seconds, cores)
+        cpu = {"value": n_done / secs, "unit": "source pts/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {pairs_done} of {P} pairs in order (their target maps built by "
+                         f"the oracle inside the timed sample), {n_done} source points, "
+                         f"{secs:.1f} s, FP64, OpenMP over {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "source pts/s", "n_gpus": world,
+            "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded city-loop submaps; no dataset available)",
+            "config": workload_config(w, args, {"parallelism": f"independent factor sets x{world}",
+                                                "tile": args.tile or 8192}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "linearize_kernel<1>", "kernel_ms": kernel_ms,
+                         "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pts,
+                         "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"},
+            "e2e": {"value": e2e_value, "unit": "source pts/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def linearize_batched_timed(api, maps, srcs, pairs, poses, out, inl, args, events=None):
+    import ctypes
+
+    from paper_2202_00242_gb300 import _lib
+    from paper_2202_00242_gb300._lib import LinOpts, check
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+    poses = np.ascontiguousarray(poses, dtype=np.float64)
+    clouds = api.make_clouds(srcs)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    ev0 = ctypes.c_void_p(events[0].cuda_event) if events is not None else None
+    ev1 = ctypes.c_void_p(events[1].cuda_event) if events is not None else None
+    opts = LinOpts(1, int(args.tile), int(args.grid), 0, None, None, ev0, ev1)
+    import torch
+    check(_lib.load().vgicp_linearize_batched(
+        arr, len(maps), clouds, len(srcs), pairs.ctypes.data_as(ctypes.c_void_p), pairs.shape[0],
+        poses.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(inl.data_ptr()), ctypes.byref(opts),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return
+    w = make_workload(args, 0)
+    cores = host_cores()
+    P = w.pairs.shape[0]
+    per_step_pairs = 4
+    for s in range(max(args.warmup, 3)):
+        oracle_sample(w, 0.0, cores, start_pair=s * per_step_pairs, min_pairs=per_step_pairs)
+    t0 = time.perf_counter()
+    pts = 0
+    for s in range(args.steps):
+        n, _, _ = oracle_sample(w, 0.0, cores, start_pair=(s * per_step_pairs) % P,
+                                min_pairs=per_step_pairs)
+        pts += n
+    secs = time.perf_counter() - t0
+    value = pts / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "source pts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded city-loop submaps; no dataset available)",
+        "config": workload_config(w, args, {"parallelism": "host cores (oracle)"}),
+        "cpu_baseline": {"value": value, "unit": "source pts/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step_pairs} consecutive pairs per step (target maps "
+                                   f"built inside the step), FP64 oracle, OpenMP over {cores} "
+                                   "threads"},
+        "e2e": {"value": value, "unit": "source pts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * vgicp.h -- C ABI of the GB300 (sm_103a) VGICP factor-linearization library.
+ *
+ * The library computes, on one GPU, the voxelized-GICP matching cost factor of
+ * arXiv 2202.00242 ("Globally Consistent and Tightly Coupled 3D LiDAR Inertial
+ * Mapping"), Sec. III-A:
+ *
+ *   e^M = sum_{p_k in P_i} d_k^T (C'_k + R C_k R^T)^-1 d_k          (Eqs. 2-3)
+ *   d_k = mu'_k - (R mu_k + t),
+ *
+ * where (mu'_k, C'_k) is the Gaussian of the voxel of the target map P_j that
+ * contains T mu_k, and its linearization into a Hessian factor (Sec. III-A, last
+ * paragraph: the factor is re-linearized at every optimizer iteration):
+ *
+ *   J_k = d d_k / d xi = [ R [mu_k]x , -R ]   for T <- T Exp(xi), xi = [omega; v]
+ *   H = sum J_k^T W_k J_k,  b = sum J_k^T W_k d_k,  err = sum d_k^T W_k d_k,
+ *   W_k = (C'_k + R C_k R^T)^-1 held at the linearization point,
+ *   so err(xi) ~ err + 2 b^T xi + xi^T H xi and the Gauss-Newton step is -H^-1 b.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an int status (VGICP_OK or a negative code) and set a
+ *     thread-local message readable with vgicp_last_error_string().
+ *   - Pointers are DEVICE pointers unless the parameter is marked "host".
+ *     The caller owns every input and output buffer; the library owns handles.
+ *   - Every call takes a cudaStream_t and is asynchronous on it unless stated
+ *     ("synchronizes").  Argument errors are reported synchronously.  Device-side
+ *     build errors (key range, hash probe limit) are recorded in the map and read
+ *     by vgicp_voxelmap_status(), which synchronizes the stream.
+ *   - Point clouds are float32 AoS: points n x 3 (x, y, z), covariances n x 6
+ *     upper triangles (xx, xy, xz, yy, yz, zz).  Both arrays must be 4-byte
+ *     aligned; 16-byte alignment of the base is recommended.
+ *   - Poses are host binary64 row-major 4x4 matrices T_target_source mapping
+ *     source coordinates into the target frame.
+ *   - A factor result is 43 doubles: H (36, row-major, symmetric), b (6), err (1).
+ */
+#ifndef VGICP_H
+#define VGICP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same underlying type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* vgicp_stream_t;
+
+enum {
+  VGICP_OK = 0,
+  VGICP_ERR_INVALID_ARG = -1, /* bad pointer, size, option or pose */
+  VGICP_ERR_OOM = -2,         /* device allocation failed */
+  VGICP_ERR_HASH_FULL = -3,   /* a voxel could not be inserted within max_probe slots */
+  VGICP_ERR_KEY_RANGE = -4,   /* |floor(x / r)| does not fit the 21-bit key field */
+  VGICP_ERR_CUDA = -5         /* a CUDA runtime call failed (message has details) */
+};
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* vgicp_last_error_string(void);
+
+/* Library version, e.g. 10000 for 1.0.0. */
+int vgicp_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads, all devices); for accounting in benchmarks. */
+int64_t vgicp_launch_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* Voxel maps (Sec. III-A: the target cloud P_j is split into voxels, and each
+ * voxel keeps one Gaussian formed from the means and covariances of the points
+ * that fall inside it).
+ *
+ * Voxel key of a point x: k = floor((double)x / resolution) per axis, computed
+ * exactly as in binary64 (a point on a face belongs to the voxel above it).
+ * Each voxel stores N, mu' = (sum mu_p) / N and C' = (sum C_p) / N, the sums
+ * taken in binary64 in ascending point index and rounded once to float32.
+ * Voxels are numbered 0..V-1 in order of first appearance in the cloud.       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct vgicp_map vgicp_map;
+
+typedef struct {
+  int32_t max_probe;       /* linear-probe limit of the hash table; 0 = 64 */
+  int32_t capacity_factor; /* table capacity = next pow2 >= factor * n; 0 = 2 */
+} vgicp_map_opts;
+
+/* Build the voxel map of one target cloud.  points: n x 3, covs: n x 6 (device,
+ * read during the call's kernels only).  resolution > 0.  n >= 0 (an empty map
+ * is valid).  *out receives a new handle.  Asynchronous; check
+ * vgicp_voxelmap_status() before relying on the contents. */
+int vgicp_build_voxelmap(const float* points, const float* covs, int64_t n, double resolution,
+                         const vgicp_map_opts* opts, vgicp_stream_t stream, vgicp_map** out);
+
+/* Build n_maps voxel maps at once from concatenated clouds: map m is built from
+ * rows offsets[m] .. offsets[m+1]-1 of points/covs.  offsets: host, n_maps + 1
+ * non-decreasing entries starting at 0.  out: host array of n_maps handles.
+ * The maps share one allocation (freed when the last handle is destroyed) and
+ * one set of build kernels. */
+int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t* offsets,
+                          int32_t n_maps, double resolution, const vgicp_map_opts* opts,
+                          vgicp_stream_t stream, vgicp_map** out);
+
+/* Rebuild maps in place from new clouds of the same sizes.  maps must be all
+ * handles of one vgicp_build_voxelmaps() call (or the single handle of
+ * vgicp_build_voxelmap()), in their original order.  No allocation. */
+int vgicp_rebuild_voxelmaps(vgicp_map* const* maps, int32_t n_maps, const float* points,
+                            const float* covs, vgicp_stream_t stream);
+
+/* Release a handle (and the storage when it is the last handle of its batch).
+ * The caller must ensure no queued kernel still reads the map. */
+int vgicp_destroy_voxelmap(vgicp_map* map);
+
+/* Synchronizes stream; returns the device-side build status of the map's batch
+ * (VGICP_OK, VGICP_ERR_HASH_FULL or VGICP_ERR_KEY_RANGE). */
+int vgicp_voxelmap_status(const vgicp_map* map, vgicp_stream_t stream);
+
+/* Synchronizes stream.  num_voxels: V of this map; capacity: hash slots. */
+int vgicp_voxelmap_info(const vgicp_map* map, vgicp_stream_t stream, int64_t* num_voxels,
+                        int64_t* capacity);
+
+/* Synchronizes stream.  Copies the voxels (first-appearance order) to host
+ * arrays of at least max_voxels rows: keys V x 3 (int64), counts V (int32),
+ * means V x 3 and covs V x 6 (float32).  Any output may be NULL. */
+int vgicp_voxelmap_export(const vgicp_map* map, vgicp_stream_t stream, int64_t max_voxels,
+                          int64_t* keys, int32_t* counts, float* means, float* covs);
+
+/* ------------------------------------------------------------------------ */
+/* Linearization (Eqs. 2-3 and the Hessian factor of Sec. III-A).             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t neighbours; /* 1: the voxel containing T mu (the paper's lookup);
+                         27: every occupied voxel of the 3x3x3 block around it,
+                         one independent term each; 0 = 1 */
+  int32_t tile;       /* source points per work item; 0 = automatic */
+  int32_t grid;       /* CTAs of the persistent launch; 0 = automatic */
+  int32_t reserved;
+  int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
+                         point's own voxel (first-appearance numbering) or -1 */
+  int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
+  void* kernel_start; /* optional cudaEvent_t recorded on the stream just before the
+                         linearize kernel is launched (for timing) */
+  void* kernel_stop;  /* optional cudaEvent_t recorded just after it */
+} vgicp_lin_opts;
+
+/* Linearize one factor.  T_target_source: host, 16 doubles.  out: device, 43
+ * doubles (H 36, b 6, err 1).  inliers: device, 1 int64 = number of source
+ * points whose voxel is occupied (the overlap rate of Sec. III-D times n_src).
+ * n_src = 0 gives zeros.  opts may be NULL. */
+int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* src_covs,
+                    int64_t n_src, const double* T_target_source, double* out, int64_t* inliers,
+                    const vgicp_lin_opts* opts, vgicp_stream_t stream);
+
+/* A source cloud for batched calls (device pointers). */
+typedef struct {
+  const float* points; /* n x 3 */
+  const float* covs;   /* n x 6 */
+  int64_t n;
+} vgicp_cloud;
+
+/* Linearize n_pairs independent factors in one persistent launch (Sec. III-F:
+ * a factor for every overlapping submap pair).  maps: host array of n_maps
+ * handles; sources: host array of n_sources clouds; pairs: host n_pairs x 2
+ * int32 (map index, source index); poses: host n_pairs x 16 doubles.  out:
+ * device n_pairs x 43; inliers: device n_pairs.  Work is split into tiles of
+ * opts->tile points so that uneven clouds balance across the GPU. */
+int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                            int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                            const double* poses, double* out, int64_t* inliers,
+                            const vgicp_lin_opts* opts, vgicp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VGICP_H */

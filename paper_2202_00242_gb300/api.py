@@ -1,0 +1,226 @@
+"""Python API over the C ABI (include/vgicp.h).  PyTorch provides device memory
+and streams; every step of the computation runs in the library's CUDA kernels.
+
+Layouts: clouds are float32 CUDA tensors, points (n, 3) and covariances (n, 6)
+upper triangles (xx, xy, xz, yy, yz, zz); poses are float64 host arrays (4, 4)
+T_target_source.  A factor result is 43 float64 values: H (36), b (6), err (1),
+see ``unpack``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Cloud, LinOpts, MapOpts, check
+
+RESULT_SIZE = 43
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_cloud(points: torch.Tensor, covs: torch.Tensor, what="cloud"):
+    if not (points.is_cuda and covs.is_cuda):
+        raise ValueError(f"{what}: tensors must be on a CUDA device")
+    if points.dtype != torch.float32 or covs.dtype != torch.float32:
+        raise ValueError(f"{what}: tensors must be float32")
+    if points.dim() != 2 or points.shape[1] != 3 or covs.dim() != 2 or covs.shape[1] != 6:
+        raise ValueError(f"{what}: expected points (n, 3) and covs (n, 6)")
+    if points.shape[0] != covs.shape[0]:
+        raise ValueError(f"{what}: points and covs differ in length")
+    if not (points.is_contiguous() and covs.is_contiguous()):
+        raise ValueError(f"{what}: tensors must be contiguous")
+
+
+def _pose_array(T, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64))
+    if n is None:
+        if a.shape != (4, 4):
+            raise ValueError("pose must be (4, 4)")
+    elif a.shape != (n, 4, 4):
+        raise ValueError(f"poses must be ({n}, 4, 4)")
+    return a
+
+
+def _map_opts(max_probe, capacity_factor):
+    return MapOpts(int(max_probe), int(capacity_factor))
+
+
+class VoxelMap:
+    """Voxel map of a target cloud on the GPU (Sec. III-A of arXiv 2202.00242)."""
+
+    def __init__(self, handle, resolution, n, refs):
+        self._h = ctypes.c_void_p(handle)
+        self.resolution = float(resolution)
+        self.n = int(n)
+        self._refs = refs  # inputs read by queued build kernels
+
+    @property
+    def handle(self):
+        return self._h
+
+    @staticmethod
+    def build(points: torch.Tensor, covs: torch.Tensor, resolution: float, max_probe=0,
+              capacity_factor=0, stream=None) -> "VoxelMap":
+        _check_cloud(points, covs, "target")
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        opts = _map_opts(max_probe, capacity_factor)
+        check(lib.vgicp_build_voxelmap(ctypes.c_void_p(points.data_ptr()),
+                                       ctypes.c_void_p(covs.data_ptr()), points.shape[0],
+                                       float(resolution), ctypes.byref(opts), _stream_ptr(stream),
+                                       ctypes.byref(h)))
+        return VoxelMap(h.value, resolution, points.shape[0], [points, covs])
+
+    def status(self, stream=None) -> int:
+        """Synchronizes; raises VGICPError on a device-side build error."""
+        return check(_lib.load().vgicp_voxelmap_status(self._h, _stream_ptr(stream)))
+
+    def info(self, stream=None):
+        V = ctypes.c_int64()
+        cap = ctypes.c_int64()
+        check(_lib.load().vgicp_voxelmap_info(self._h, _stream_ptr(stream), ctypes.byref(V),
+                                              ctypes.byref(cap)))
+        return int(V.value), int(cap.value)
+
+    @property
+    def num_voxels(self) -> int:
+        return self.info()[0]
+
+    def export(self, stream=None) -> dict:
+        V, _ = self.info(stream)
+        keys = np.zeros((max(V, 1), 3), np.int64)
+        counts = np.zeros(max(V, 1), np.int32)
+        means = np.zeros((max(V, 1), 3), np.float32)
+        covs = np.zeros((max(V, 1), 6), np.float32)
+        check(_lib.load().vgicp_voxelmap_export(
+            self._h, _stream_ptr(stream), max(V, 1), keys.ctypes.data_as(ctypes.c_void_p),
+            counts.ctypes.data_as(ctypes.c_void_p), means.ctypes.data_as(ctypes.c_void_p),
+            covs.ctypes.data_as(ctypes.c_void_p)))
+        return {"keys": keys[:V], "counts": counts[:V], "means": means[:V], "covs": covs[:V]}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.load().vgicp_destroy_voxelmap(self._h)
+        self._h = None
+        self._refs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_voxelmaps(points: torch.Tensor, covs: torch.Tensor, offsets, resolution: float,
+                    max_probe=0, capacity_factor=0, stream=None) -> list[VoxelMap]:
+    """Build one map per cloud of a concatenation (rows offsets[m]:offsets[m+1])."""
+    _check_cloud(points, covs, "targets")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    n_maps = off.shape[0] - 1
+    if n_maps < 1 or off[0] != 0 or off[-1] != points.shape[0]:
+        raise ValueError("offsets must start at 0 and end at the number of points")
+    handles = (ctypes.c_void_p * n_maps)()
+    opts = _map_opts(max_probe, capacity_factor)
+    check(_lib.load().vgicp_build_voxelmaps(ctypes.c_void_p(points.data_ptr()),
+                                            ctypes.c_void_p(covs.data_ptr()),
+                                            off.ctypes.data_as(ctypes.c_void_p), n_maps,
+                                            float(resolution), ctypes.byref(opts),
+                                            _stream_ptr(stream), handles))
+    refs = [points, covs]
+    return [VoxelMap(handles[m], resolution, off[m + 1] - off[m], refs) for m in range(n_maps)]
+
+
+def rebuild_voxelmaps(maps: list[VoxelMap], points: torch.Tensor, covs: torch.Tensor,
+                      stream=None):
+    """Refill a batch of maps (all handles of one build, in order) from new clouds of
+    the same sizes; allocates nothing."""
+    _check_cloud(points, covs, "targets")
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    check(_lib.load().vgicp_rebuild_voxelmaps(arr, len(maps), ctypes.c_void_p(points.data_ptr()),
+                                              ctypes.c_void_p(covs.data_ptr()),
+                                              _stream_ptr(stream)))
+    for m in maps:
+        m._refs = [points, covs]
+
+
+@dataclass
+class Linearization:
+    out: torch.Tensor       # (43,) or (P, 43) float64, device
+    inliers: torch.Tensor   # () or (P,) int64, device
+    corr: torch.Tensor | None = None
+    qkeys: torch.Tensor | None = None
+
+    def unpack(self):
+        return unpack(self.out)
+
+
+def unpack(out):
+    """Split (..., 43) results into H (..., 6, 6), b (..., 6), err (...)."""
+    H = out[..., :36].reshape(*out.shape[:-1], 6, 6)
+    return H, out[..., 36:42], out[..., 42]
+
+
+def linearize(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T, neighbours=1, tile=0,
+              grid=0, corr=False, qkeys=False, out=None, inliers=None,
+              stream=None) -> Linearization:
+    """Linearize one factor at T = T_target_source (Eqs. 2-3 of arXiv 2202.00242)."""
+    _check_cloud(points, covs, "source")
+    dev = points.device
+    T = _pose_array(T)
+    n = points.shape[0]
+    if out is None:
+        out = torch.empty(RESULT_SIZE, dtype=torch.float64, device=dev)
+    if inliers is None:
+        inliers = torch.empty((), dtype=torch.int64, device=dev)
+    c = torch.empty(n, dtype=torch.int32, device=dev) if corr else None
+    q = torch.empty((n, 3), dtype=torch.int32, device=dev) if qkeys else None
+    opts = LinOpts(int(neighbours), int(tile), int(grid), 0,
+                   ctypes.c_void_p(c.data_ptr()) if c is not None else None,
+                   ctypes.c_void_p(q.data_ptr()) if q is not None else None)
+    check(_lib.load().vgicp_linearize(vmap.handle, ctypes.c_void_p(points.data_ptr()),
+                                      ctypes.c_void_p(covs.data_ptr()), n,
+                                      T.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(inliers.data_ptr()), ctypes.byref(opts),
+                                      _stream_ptr(stream)))
+    return Linearization(out, inliers, c, q)
+
+
+def make_clouds(sources) -> tuple:
+    """ctypes array of vgicp_cloud from a list of (points, covs) tensors."""
+    arr = (Cloud * len(sources))()
+    for i, (p, c) in enumerate(sources):
+        _check_cloud(p, c, f"source {i}")
+        arr[i] = Cloud(p.data_ptr(), c.data_ptr(), p.shape[0])
+    return arr
+
+
+def linearize_batched(maps: list[VoxelMap], sources, pairs, poses, neighbours=1, tile=0, grid=0,
+                      out=None, inliers=None, stream=None) -> Linearization:
+    """Linearize many factors in one persistent launch.  sources: list of (points,
+    covs); pairs: (P, 2) int (map index, source index); poses: (P, 4, 4)."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0]
+    poses = _pose_array(poses, P)
+    dev = sources[0][0].device
+    if out is None:
+        out = torch.empty((P, RESULT_SIZE), dtype=torch.float64, device=dev)
+    if inliers is None:
+        inliers = torch.empty(P, dtype=torch.int64, device=dev)
+    clouds = make_clouds(sources)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    opts = LinOpts(int(neighbours), int(tile), int(grid), 0, None, None)
+    check(_lib.load().vgicp_linearize_batched(arr, len(maps), clouds, len(sources),
+                                              pairs.ctypes.data_as(ctypes.c_void_p), P,
+                                              poses.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.c_void_p(out.data_ptr()),
+                                              ctypes.c_void_p(inliers.data_ptr()),
+                                              ctypes.byref(opts), _stream_ptr(stream)))
+    return Linearization(out, inliers)

@@ -1,0 +1,536 @@
+// Host runtime and C ABI of the VGICP library: map handles and their storage,
+// argument checking, pose conversion, the batched work planner, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "vgicp.h"
+#include "vgicp_internal.h"
+
+namespace vgicp {
+
+namespace {
+thread_local std::string g_error;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 16;
+  while (p < x) p <<= 1;
+  return (uint32_t)p;
+}
+
+bool finite_pose(const double* T) {
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(T[i])) return false;
+  if (T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0) return false;
+  // R^T R = I and det R = +1 within float32-level tolerance
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += T[4 * k + i] * T[4 * k + j];
+      if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 1e-5) return false;
+    }
+  double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
+               T[2] * (T[4] * T[9] - T[5] * T[8]);
+  return det > 0.0;
+}
+
+PairDesc make_pair_desc(const double* T, int32_t map, int32_t src) {
+  PairDesc p;
+  std::memset(&p, 0, sizeof(p));
+  double tmax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      p.R[3 * i + j] = (float)T[4 * i + j];
+      p.R64[3 * i + j] = T[4 * i + j];
+    }
+    p.t[i] = (float)T[4 * i + 3];
+    p.t64[i] = T[4 * i + 3];
+    tmax = std::max(tmax, std::fabs(T[4 * i + 3]));
+  }
+  float tm = (float)tmax;
+  if ((double)tm < tmax) tm = std::nextafter(tm, INFINITY);
+  p.tmax = tm;
+  p.map = map;
+  p.src = src;
+  return p;
+}
+
+MapDesc make_map_desc(const vgicp_map* m) {
+  const MapSet* s = m->set;
+  MapDesc d;
+  d.slots = s->d_slots + s->slot_base[m->index];
+  d.recs = s->d_recs;
+  d.mask = s->cap[m->index] - 1u;
+  d.max_probe = s->max_probe;
+  d.inv_r = (float)(1.0 / s->resolution);
+  d.margin_scale = d.inv_r * 4.76837158203125e-7f;  // 2^-21
+  d.r = s->resolution;
+  d.vbase = s->d_vbase + m->index;
+  return d;
+}
+
+int check_cloud(const float* pts, const float* covs, int64_t n, const char* what) {
+  if (n < 0) return set_error(VGICP_ERR_INVALID_ARG, std::string(what) + ": negative size");
+  if (n > INT32_MAX)
+    return set_error(VGICP_ERR_INVALID_ARG, std::string(what) + ": more than 2^31-1 points");
+  if (n > 0 && (!pts || !covs))
+    return set_error(VGICP_ERR_INVALID_ARG, std::string(what) + ": null pointer");
+  if (((uintptr_t)pts & 3u) || ((uintptr_t)covs & 7u))
+    return set_error(VGICP_ERR_INVALID_ARG,
+                     std::string(what) + ": points must be 4-byte and covs 8-byte aligned");
+  return VGICP_OK;
+}
+
+int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
+               const vgicp_map_opts* opts, cudaStream_t st, MapSet** out) {
+  if (!(resolution > 0.0) || !std::isfinite(resolution))
+    return set_error(VGICP_ERR_INVALID_ARG, "resolution must be positive and finite");
+  if (n_maps <= 0 || !offsets) return set_error(VGICP_ERR_INVALID_ARG, "n_maps must be >= 1");
+  if (offsets[0] != 0) return set_error(VGICP_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (int32_t m = 0; m < n_maps; ++m)
+    if (offsets[m + 1] < offsets[m])
+      return set_error(VGICP_ERR_INVALID_ARG, "offsets must be non-decreasing");
+  int32_t max_probe = opts && opts->max_probe > 0 ? opts->max_probe : 64;
+  int32_t cf = opts && opts->capacity_factor > 0 ? opts->capacity_factor : 2;
+  if (cf > 64) return set_error(VGICP_ERR_INVALID_ARG, "capacity_factor too large");
+
+  MapSet* s = new MapSet();
+  s->n_maps = n_maps;
+  s->resolution = resolution;
+  s->max_probe = max_probe;
+  s->point_off.assign(offsets, offsets + n_maps + 1);
+  s->n_total = offsets[n_maps];
+  s->slot_base.resize(n_maps);
+  s->cap.resize(n_maps);
+  int64_t cap_total = 0;
+  for (int32_t m = 0; m < n_maps; ++m) {
+    int64_t n = offsets[m + 1] - offsets[m];
+    uint32_t c = next_pow2((uint64_t)std::max<int64_t>(n, 1) * (uint64_t)cf);
+    s->cap[m] = c;
+    s->slot_base[m] = cap_total;
+    cap_total += c;
+  }
+  s->cap_total = cap_total;
+  if (s->n_total >= (int64_t)0xFFFFFFFFll || cap_total >= (int64_t)0xFFFFFFFFll) {
+    delete s;
+    return set_error(VGICP_ERR_INVALID_ARG, "more than 2^32-1 points or slots in one batch");
+  }
+  const int64_t n = s->n_total;
+  s->scan_tmp_elems = scan_tmp_elems(std::max<int64_t>(n, 1));
+  // one allocation, 256-B aligned sub-buffers
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return o;
+  };
+  const size_t o_point_off = take(sizeof(int64_t) * (n_maps + 1));
+  const size_t o_slot_base = take(sizeof(int64_t) * n_maps);
+  const size_t o_cap_mask = take(sizeof(uint32_t) * n_maps);
+  const size_t o_vbase = take(sizeof(uint32_t) * (n_maps + 1));
+  const size_t o_slots = take(sizeof(Slot) * cap_total);
+  const size_t o_recs = take(sizeof(float4) * kRecordF4 * n);
+  const size_t o_vkeys = take(sizeof(unsigned long long) * n);
+  const size_t o_status = take(sizeof(int32_t));
+  const size_t o_num_vox = take(sizeof(uint32_t));
+  const size_t o_pt_slot = take(sizeof(uint32_t) * n);
+  const size_t o_flag = take(sizeof(uint32_t) * n);
+  const size_t o_vcount = take(sizeof(uint32_t) * n);
+  const size_t o_voff = take(sizeof(uint32_t) * n);
+  const size_t o_vfill = take(sizeof(uint32_t) * n);
+  const size_t o_plist = take(sizeof(uint32_t) * n);
+  const size_t o_scan = take(sizeof(uint32_t) * s->scan_tmp_elems);
+  cudaError_t e = cudaMalloc(&s->d_block, off);
+  if (e != cudaSuccess) {
+    delete s;
+    cudaGetLastError();
+    return set_error(VGICP_ERR_OOM, std::string("voxel map allocation of ") +
+                                        std::to_string(off) + " bytes failed");
+  }
+  char* b = static_cast<char*>(s->d_block);
+  s->d_point_off = reinterpret_cast<int64_t*>(b + o_point_off);
+  s->d_slot_base = reinterpret_cast<int64_t*>(b + o_slot_base);
+  s->d_cap_mask = reinterpret_cast<uint32_t*>(b + o_cap_mask);
+  s->d_vbase = reinterpret_cast<uint32_t*>(b + o_vbase);
+  s->d_slots = reinterpret_cast<Slot*>(b + o_slots);
+  s->d_recs = reinterpret_cast<float4*>(b + o_recs);
+  s->d_vkeys = reinterpret_cast<unsigned long long*>(b + o_vkeys);
+  s->d_status = reinterpret_cast<int32_t*>(b + o_status);
+  s->d_num_voxels = reinterpret_cast<uint32_t*>(b + o_num_vox);
+  s->d_pt_slot = reinterpret_cast<uint32_t*>(b + o_pt_slot);
+  s->d_flag = reinterpret_cast<uint32_t*>(b + o_flag);
+  s->d_vcount = reinterpret_cast<uint32_t*>(b + o_vcount);
+  s->d_voff = reinterpret_cast<uint32_t*>(b + o_voff);
+  s->d_vfill = reinterpret_cast<uint32_t*>(b + o_vfill);
+  s->d_plist = reinterpret_cast<uint32_t*>(b + o_plist);
+  s->d_scan_tmp = reinterpret_cast<uint32_t*>(b + o_scan);
+  cudaGetDevice(&s->device);
+  std::vector<uint32_t> mask(n_maps);
+  for (int32_t m = 0; m < n_maps; ++m) mask[m] = s->cap[m] - 1u;
+  // metadata is small: synchronous copies keep the host vectors' lifetime simple
+  e = cudaMemcpy(s->d_point_off, s->point_off.data(), sizeof(int64_t) * (n_maps + 1),
+                 cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_slot_base, s->slot_base.data(), sizeof(int64_t) * n_maps,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_cap_mask, mask.data(), sizeof(uint32_t) * n_maps, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_block);
+    delete s;
+    return check_cuda(e, "cudaMemcpy(map metadata)");
+  }
+  (void)st;
+  *out = s;
+  return VGICP_OK;
+}
+
+void release_set(MapSet* s) {
+  if (--s->refcount == 0) {
+    cudaFree(s->d_block);
+    delete s;
+  }
+}
+
+int sm_count_cache[64] = {0};
+std::mutex sm_mutex;
+std::atomic<int64_t> g_launches{0};
+
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+int check_cuda(cudaError_t e, const char* what) {
+  g_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return VGICP_ERR_CUDA;
+}
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> g(sm_mutex);
+  if (sm_count_cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+    sm_count_cache[dev] = n;
+  }
+  return sm_count_cache[dev];
+}
+
+}  // namespace vgicp
+
+using namespace vgicp;
+
+extern "C" {
+
+const char* vgicp_last_error_string(void) { return g_error.c_str(); }
+
+int vgicp_version(void) { return 10000; }
+
+int64_t vgicp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t* offsets,
+                          int32_t n_maps, double resolution, const vgicp_map_opts* opts,
+                          vgicp_stream_t stream, vgicp_map** out) {
+  g_error.clear();
+  if (!out) return set_error(VGICP_ERR_INVALID_ARG, "out is null");
+  if (n_maps <= 0 || !offsets) return set_error(VGICP_ERR_INVALID_ARG, "n_maps must be >= 1");
+  int rc = check_cloud(points, covs, offsets[n_maps], "target clouds");
+  if (rc) return rc;
+  MapSet* s = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  rc = create_set(offsets, n_maps, resolution, opts, st, &s);
+  if (rc) return rc;
+  rc = launch_build(s, points, covs, st);
+  if (rc) {
+    cudaFree(s->d_block);
+    delete s;
+    return rc;
+  }
+  for (int32_t m = 0; m < n_maps; ++m) {
+    out[m] = new vgicp_map{s, m};
+    ++s->refcount;
+  }
+  return VGICP_OK;
+}
+
+int vgicp_build_voxelmap(const float* points, const float* covs, int64_t n, double resolution,
+                         const vgicp_map_opts* opts, vgicp_stream_t stream, vgicp_map** out) {
+  if (n < 0) return set_error(VGICP_ERR_INVALID_ARG, "negative size");
+  const int64_t off[2] = {0, n};
+  return vgicp_build_voxelmaps(points, covs, off, 1, resolution, opts, stream, out);
+}
+
+int vgicp_rebuild_voxelmaps(vgicp_map* const* maps, int32_t n_maps, const float* points,
+                            const float* covs, vgicp_stream_t stream) {
+  g_error.clear();
+  if (!maps || n_maps <= 0 || !maps[0]) return set_error(VGICP_ERR_INVALID_ARG, "no maps");
+  MapSet* s = maps[0]->set;
+  if (n_maps != s->n_maps)
+    return set_error(VGICP_ERR_INVALID_ARG, "rebuild needs every map of the batch");
+  for (int32_t m = 0; m < n_maps; ++m)
+    if (!maps[m] || maps[m]->set != s || maps[m]->index != m)
+      return set_error(VGICP_ERR_INVALID_ARG, "maps are not one batch in creation order");
+  int rc = check_cloud(points, covs, s->n_total, "target clouds");
+  if (rc) return rc;
+  return launch_build(s, points, covs, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int vgicp_destroy_voxelmap(vgicp_map* map) {
+  g_error.clear();
+  if (!map) return VGICP_OK;
+  release_set(map->set);
+  delete map;
+  return VGICP_OK;
+}
+
+int vgicp_voxelmap_status(const vgicp_map* map, vgicp_stream_t stream) {
+  g_error.clear();
+  if (!map) return set_error(VGICP_ERR_INVALID_ARG, "map is null");
+  VGICP_CUDA_TRY(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  int32_t st = 0;
+  VGICP_CUDA_TRY(cudaMemcpy(&st, map->set->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st == VGICP_ERR_HASH_FULL)
+    return set_error(st, "voxel map build: a voxel did not fit within max_probe slots");
+  if (st == VGICP_ERR_KEY_RANGE)
+    return set_error(st, "voxel map build: a point's voxel key is outside [-2^20, 2^20) "
+                         "(coordinate too large for the resolution, or not finite)");
+  return st;
+}
+
+int vgicp_voxelmap_info(const vgicp_map* map, vgicp_stream_t stream, int64_t* num_voxels,
+                        int64_t* capacity) {
+  g_error.clear();
+  if (!map) return set_error(VGICP_ERR_INVALID_ARG, "map is null");
+  VGICP_CUDA_TRY(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  uint32_t vb[2];
+  VGICP_CUDA_TRY(cudaMemcpy(vb, map->set->d_vbase + map->index, sizeof(vb),
+                            cudaMemcpyDeviceToHost));
+  if (num_voxels) *num_voxels = (int64_t)vb[1] - (int64_t)vb[0];
+  if (capacity) *capacity = map->set->cap[map->index];
+  return VGICP_OK;
+}
+
+int vgicp_voxelmap_export(const vgicp_map* map, vgicp_stream_t stream, int64_t max_voxels,
+                          int64_t* keys, int32_t* counts, float* means, float* covs) {
+  int64_t V = 0;
+  int rc = vgicp_voxelmap_info(map, stream, &V, nullptr);
+  if (rc) return rc;
+  if (V > max_voxels) return set_error(VGICP_ERR_INVALID_ARG, "max_voxels smaller than V");
+  if (V == 0) return VGICP_OK;
+  const MapSet* s = map->set;
+  uint32_t vb = 0;
+  VGICP_CUDA_TRY(cudaMemcpy(&vb, s->d_vbase + map->index, sizeof(vb), cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> k((size_t)V);
+  std::vector<float4> r((size_t)V * kRecordF4);
+  VGICP_CUDA_TRY(cudaMemcpy(k.data(), s->d_vkeys + vb, sizeof(unsigned long long) * V,
+                            cudaMemcpyDeviceToHost));
+  VGICP_CUDA_TRY(cudaMemcpy(r.data(), s->d_recs + (size_t)vb * kRecordF4,
+                            sizeof(float4) * kRecordF4 * V, cudaMemcpyDeviceToHost));
+  const unsigned long long fm = (1ull << kKeyBits) - 1ull;
+  for (int64_t v = 0; v < V; ++v) {
+    if (keys) {
+      keys[3 * v + 0] = (int64_t)((k[v] >> (2 * kKeyBits)) & fm) - kKeyBias;
+      keys[3 * v + 1] = (int64_t)((k[v] >> kKeyBits) & fm) - kKeyBias;
+      keys[3 * v + 2] = (int64_t)(k[v] & fm) - kKeyBias;
+    }
+    const float4 a = r[3 * v], b = r[3 * v + 1], c = r[3 * v + 2];
+    if (counts) {
+      uint32_t cnt;
+      std::memcpy(&cnt, &a.w, sizeof(cnt));
+      counts[v] = (int32_t)cnt;
+    }
+    if (means) {
+      means[3 * v + 0] = a.x;
+      means[3 * v + 1] = a.y;
+      means[3 * v + 2] = a.z;
+    }
+    if (covs) {
+      covs[6 * v + 0] = b.x;
+      covs[6 * v + 1] = b.y;
+      covs[6 * v + 2] = b.z;
+      covs[6 * v + 3] = b.w;
+      covs[6 * v + 4] = c.x;
+      covs[6 * v + 5] = c.y;
+    }
+  }
+  return VGICP_OK;
+}
+
+int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* src_covs,
+                    int64_t n_src, const double* T_target_source, double* out, int64_t* inliers,
+                    const vgicp_lin_opts* opts, vgicp_stream_t stream) {
+  g_error.clear();
+  if (!map || !out || !inliers || !T_target_source)
+    return set_error(VGICP_ERR_INVALID_ARG, "null map, output or pose");
+  int rc = check_cloud(src_points, src_covs, n_src, "source cloud");
+  if (rc) return rc;
+  if (!finite_pose(T_target_source))
+    return set_error(VGICP_ERR_INVALID_ARG, "pose must be a finite rigid transform");
+  const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
+  if (neighbours != 1 && neighbours != 27)
+    return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  int tile = opts && opts->tile > 0 ? opts->tile : 0;
+  if (tile == 0) {
+    const int64_t target_items = (int64_t)device_sm_count() * 2;
+    int64_t t = (n_src + target_items - 1) / std::max<int64_t>(target_items, 1);
+    t = std::max<int64_t>(256, std::min<int64_t>(8192, (t + 255) / 256 * 256));
+    tile = (int)t;
+  }
+  const int32_t n_items = (int32_t)((n_src + tile - 1) / tile);
+
+  LinLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.items = nullptr;
+  L.n_items = n_items;
+  L.tile = tile;
+  L.single = make_pair_desc(T_target_source, 0, 0);
+  L.single_map = make_map_desc(map);
+  L.single_src = SrcDesc{src_points, src_covs, n_src};
+  L.corr_out = opts ? opts->corr_out : nullptr;
+  L.qkey_out = opts ? opts->qkey_out : nullptr;
+  L.neighbours = neighbours;
+  L.grid = opts ? opts->grid : 0;
+  L.block = 0;
+  L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
+  L.ev_stop = opts ? static_cast<cudaEvent_t>(opts->kernel_stop) : nullptr;
+  double* partials = nullptr;
+  if (n_items > 0) {
+    VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&partials),
+                                   sizeof(double) * kPartialStride * n_items, st));
+  }
+  L.partials = partials;
+  rc = launch_linearize(L, st);
+  if (rc == VGICP_OK) rc = launch_reduce(partials, nullptr, n_items, 1, out, inliers, st);
+  if (partials) {
+    cudaError_t e = cudaFreeAsync(partials, st);
+    if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");
+  }
+  return rc;
+}
+
+int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                            int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                            const double* poses, double* out, int64_t* inliers,
+                            const vgicp_lin_opts* opts, vgicp_stream_t stream) {
+  g_error.clear();
+  if (n_pairs < 0) return set_error(VGICP_ERR_INVALID_ARG, "negative n_pairs");
+  if (n_pairs == 0) return VGICP_OK;
+  if (!maps || n_maps <= 0 || !sources || n_sources <= 0 || !pairs || !poses || !out || !inliers)
+    return set_error(VGICP_ERR_INVALID_ARG, "null argument");
+  if (n_pairs > INT32_MAX / 2) return set_error(VGICP_ERR_INVALID_ARG, "too many pairs");
+  const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
+  if (neighbours != 1 && neighbours != 27)
+    return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
+  if (opts && (opts->corr_out || opts->qkey_out))
+    return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
+  for (int32_t m = 0; m < n_maps; ++m)
+    if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
+  for (int32_t c = 0; c < n_sources; ++c) {
+    int rc = check_cloud(sources[c].points, sources[c].covs, sources[c].n, "source cloud");
+    if (rc) return rc;
+  }
+  const int tile = opts && opts->tile > 0 ? opts->tile : 8192;
+  // host planner: pair descriptors, work items (tiles of each pair's source)
+  std::vector<PairDesc> pd((size_t)n_pairs);
+  std::vector<int32_t> item_off((size_t)n_pairs + 1);
+  std::vector<WorkItem> items;
+  int64_t n_items = 0;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    const int32_t m = pairs[2 * p], c = pairs[2 * p + 1];
+    if (m < 0 || m >= n_maps || c < 0 || c >= n_sources)
+      return set_error(VGICP_ERR_INVALID_ARG, "pair index out of range");
+    if (!finite_pose(poses + 16 * p))
+      return set_error(VGICP_ERR_INVALID_ARG,
+                       "pose " + std::to_string(p) + " is not a finite rigid transform");
+    pd[(size_t)p] = make_pair_desc(poses + 16 * p, m, c);
+    item_off[(size_t)p] = (int32_t)n_items;
+    n_items += (sources[c].n + tile - 1) / tile;
+  }
+  item_off[(size_t)n_pairs] = (int32_t)n_items;
+  if (n_items > INT32_MAX) return set_error(VGICP_ERR_INVALID_ARG, "too many work items");
+  items.resize((size_t)n_items);
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    const int64_t n = sources[pairs[2 * p + 1]].n;
+    int32_t k = item_off[(size_t)p];
+    for (int64_t b = 0; b < n; b += tile, ++k)
+      items[(size_t)k] = WorkItem{(int32_t)p, (int32_t)b, (int32_t)std::min<int64_t>(n, b + tile), 0};
+  }
+  std::vector<MapDesc> md((size_t)n_maps);
+  for (int32_t m = 0; m < n_maps; ++m) md[(size_t)m] = make_map_desc(maps[m]);
+  std::vector<SrcDesc> sd((size_t)n_sources);
+  for (int32_t c = 0; c < n_sources; ++c)
+    sd[(size_t)c] = SrcDesc{sources[c].points, sources[c].covs, sources[c].n};
+
+  // one device buffer: descriptors, items, offsets, partials
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return o;
+  };
+  const size_t o_pd = take(sizeof(PairDesc) * pd.size());
+  const size_t o_md = take(sizeof(MapDesc) * md.size());
+  const size_t o_sd = take(sizeof(SrcDesc) * sd.size());
+  const size_t o_items = take(sizeof(WorkItem) * items.size());
+  const size_t o_ioff = take(sizeof(int32_t) * item_off.size());
+  const size_t upload = off;
+  const size_t o_part = take(sizeof(double) * kPartialStride * std::max<int64_t>(n_items, 1));
+  std::vector<char> host(upload);
+  std::memcpy(host.data() + o_pd, pd.data(), sizeof(PairDesc) * pd.size());
+  std::memcpy(host.data() + o_md, md.data(), sizeof(MapDesc) * md.size());
+  std::memcpy(host.data() + o_sd, sd.data(), sizeof(SrcDesc) * sd.size());
+  if (!items.empty())
+    std::memcpy(host.data() + o_items, items.data(), sizeof(WorkItem) * items.size());
+  std::memcpy(host.data() + o_ioff, item_off.data(), sizeof(int32_t) * item_off.size());
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* dev = nullptr;
+  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dev), off, st));
+  int rc = VGICP_OK;
+  cudaError_t e = cudaMemcpyAsync(dev, host.data(), upload, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = check_cuda(e, "cudaMemcpyAsync(plan)");
+  // (a copy from pageable memory returns once the source has been staged, so
+  // `host` may be released when this function returns)
+  if (rc == VGICP_OK) {
+    LinLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.items = reinterpret_cast<const WorkItem*>(dev + o_items);
+    L.n_items = (int32_t)n_items;
+    L.pairs = reinterpret_cast<const PairDesc*>(dev + o_pd);
+    L.maps = reinterpret_cast<const MapDesc*>(dev + o_md);
+    L.srcs = reinterpret_cast<const SrcDesc*>(dev + o_sd);
+    L.partials = reinterpret_cast<double*>(dev + o_part);
+    L.neighbours = neighbours;
+    L.grid = opts ? opts->grid : 0;
+    L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
+    L.ev_stop = opts ? static_cast<cudaEvent_t>(opts->kernel_stop) : nullptr;
+    rc = launch_linearize(L, st);
+    if (rc == VGICP_OK)
+      rc = launch_reduce(L.partials, reinterpret_cast<const int32_t*>(dev + o_ioff), 0, n_pairs,
+                         out, inliers, st);
+  }
+  e = cudaFreeAsync(dev, st);
+  if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");
+  return rc;
+}
+
+}  // extern "C"

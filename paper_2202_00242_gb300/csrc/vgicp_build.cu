@@ -1,0 +1,352 @@
+// Voxel-map build kernels (arXiv 2202.00242 Sec. III-A: the target cloud is
+// discretised into voxels; each voxel aggregates the means and covariances of
+// its points).
+//
+// Pipeline for a batch of maps built from concatenated clouds (one launch per
+// step for the whole batch):
+//   init      table slots <- empty
+//   insert    per point: exact key, open-addressing insert (CAS on the 64-bit
+//             key, bounded linear probe), count, smallest point index
+//   first     per point: 1 if it is the smallest index of its voxel
+//   scan      voxel id = number of first points before it (so voxels are
+//             numbered in order of first appearance, map by map)
+//   assign    per first point: voxel count, key; slot.vid <- voxel id
+//   scan      voxel offsets into the point list
+//   scatter   per point: append its index to its voxel's list
+//   finalize  per voxel: sort its list, sum means and covariances in binary64
+//             in ascending point index, divide by N, round to float32
+// The result is deterministic and bit-identical to the binary64 definition
+// rounded once to float32.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "vgicp_device.cuh"
+#include "vgicp_internal.h"
+
+namespace vgicp {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int find_map(const int64_t* __restrict__ off, int32_t n_maps,
+                                        int64_t i) {
+  // last m with off[m] <= i (empty maps are skipped)
+  int lo = 0, hi = n_maps;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+  atomicCAS(status, 0, code);
+}
+
+__global__ void init_slots_kernel(Slot* __restrict__ slots, int64_t cap_total) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < cap_total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    Slot e;
+    e.key = kEmptyKey;
+    e.vid = 0xFFFFFFFFu;
+    e.count = 0u;
+    slots[s] = e;
+  }
+}
+
+__global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
+                              const int64_t* __restrict__ point_off, int32_t n_maps,
+                              const int64_t* __restrict__ slot_base,
+                              const uint32_t* __restrict__ cap_mask, float inv_r, double r,
+                              int32_t max_probe, Slot* slots, uint32_t* __restrict__ pt_slot,
+                              int32_t* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = find_map(point_off, n_maps, i);
+    const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
+    const int kx = axis_key_target(__ldg(pts + 3 * i + 0), inv_r, r);
+    const int ky = axis_key_target(__ldg(pts + 3 * i + 1), inv_r, r);
+    const int kz = axis_key_target(__ldg(pts + 3 * i + 2), inv_r, r);
+    if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) {
+      pt_slot[i] = kNoSlot;
+      set_status(status, VGICP_ERR_KEY_RANGE);
+      continue;
+    }
+    const unsigned long long key = pack_key(kx, ky, kz);
+    const uint32_t mask = __ldg(cap_mask + m);
+    const int64_t base = __ldg(slot_base + m);
+    uint32_t h = hash_key(kx, ky, kz) & mask;
+    uint32_t found = kNoSlot;
+    for (int p = 0; p < max_probe; ++p) {
+      Slot* s = slots + base + h;
+      unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&s->key);
+      if (cur == kEmptyKey) {
+        cur = atomicCAS(&s->key, kEmptyKey, key);
+        if (cur == kEmptyKey) cur = key;
+      }
+      if (cur == key) {
+        found = (uint32_t)(base + h);
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    if (found == kNoSlot) {
+      pt_slot[i] = kNoSlot;
+      set_status(status, VGICP_ERR_HASH_FULL);
+      continue;
+    }
+    atomicAdd(&slots[found].count, 1u);
+    atomicMin(&slots[found].vid, li);
+    pt_slot[i] = found;
+  }
+}
+
+__global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_off,
+                             int32_t n_maps, const Slot* __restrict__ slots,
+                             const uint32_t* __restrict__ pt_slot, uint32_t* __restrict__ first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = pt_slot[i];
+    uint32_t f = 0;
+    if (s != kNoSlot) {
+      const int m = find_map(point_off, n_maps, i);
+      const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
+      f = (slots[s].vid == li) ? 1u : 0u;
+    }
+    first[i] = f;
+  }
+}
+
+__global__ void assign_kernel(int64_t n_total, const uint32_t* __restrict__ first,
+                              const uint32_t* __restrict__ vid, const uint32_t* __restrict__ pt_slot,
+                              Slot* slots, uint32_t* __restrict__ vcount,
+                              unsigned long long* __restrict__ vkeys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!first[i]) continue;
+    const uint32_t v = vid[i];
+    Slot* s = slots + pt_slot[i];
+    vcount[v] = s->count;
+    vkeys[v] = s->key;
+    s->vid = v;
+  }
+}
+
+__global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __restrict__ point_off,
+                             const uint32_t* __restrict__ vid, const uint32_t* __restrict__ n_vox,
+                             uint32_t* __restrict__ vbase) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > n_maps) return;
+  int64_t o = point_off[m];
+  vbase[m] = (o < n_total) ? vid[o] : *n_vox;
+}
+
+__global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot,
+                               const Slot* __restrict__ slots, const uint32_t* __restrict__ voff,
+                               uint32_t* vfill, uint32_t* __restrict__ plist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = pt_slot[i];
+    if (s == kNoSlot) continue;
+    const uint32_t v = slots[s].vid;
+    const uint32_t pos = voff[v] + atomicAdd(vfill + v, 1u);
+    plist[pos] = (uint32_t)i;
+  }
+}
+
+__global__ void finalize_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
+                                const float* __restrict__ pts, const float* __restrict__ covs,
+                                const uint32_t* __restrict__ vcount,
+                                const uint32_t* __restrict__ voff, uint32_t* __restrict__ plist,
+                                float4* __restrict__ recs) {
+  const int64_t V = *n_vox;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = vcount[v];
+    uint32_t* L = plist + voff[v];
+    // ascending point index (lists are short: a voxel holds a handful of points)
+    for (uint32_t a = 1; a < c; ++a) {
+      uint32_t x = L[a];
+      int b = (int)a - 1;
+      while (b >= 0 && L[b] > x) {
+        L[b + 1] = L[b];
+        --b;
+      }
+      L[b + 1] = x;
+    }
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t a = 0; a < c; ++a) {
+      const int64_t j = L[a];
+      s[0] = __dadd_rn(s[0], (double)__ldg(pts + 3 * j + 0));
+      s[1] = __dadd_rn(s[1], (double)__ldg(pts + 3 * j + 1));
+      s[2] = __dadd_rn(s[2], (double)__ldg(pts + 3 * j + 2));
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s[3 + k] = __dadd_rn(s[3 + k], (double)__ldg(covs + 6 * j + k));
+    }
+    const double N = (double)c;
+    float f[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = __double2float_rn(__ddiv_rn(s[k], N));
+    recs[3 * v + 0] = make_float4(f[0], f[1], f[2], __uint_as_float(c));
+    recs[3 * v + 1] = make_float4(f[3], f[4], f[5], f[6]);
+    recs[3 * v + 2] = make_float4(f[7], f[8], 0.0f, 0.0f);
+  }
+}
+
+// ---- exclusive scan of uint32 (three phases) --------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+
+__device__ __forceinline__ int64_t scan_len(int64_t n_max, const uint32_t* n_dev) {
+  return n_dev ? min(n_max, (int64_t)*n_dev) : n_max;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the thread's
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t* total) {
+  __shared__ uint32_t warp_sum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t ws = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
+    uint32_t wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kScanThreads / 32) warp_sum[lane] = wi - ws;
+    if (lane == kScanThreads / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  uint32_t r = warp_sum[w] + inc - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void scan_tile_sums_kernel(const uint32_t* __restrict__ in, int64_t n_max,
+                                      const uint32_t* n_dev, uint32_t* __restrict__ sums) {
+  const int64_t n = scan_len(n_max, n_dev);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k)
+    if (base + k < n) s += in[base + k];
+  __shared__ uint32_t total;
+  block_exclusive(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(uint32_t* __restrict__ sums, int64_t nb,
+                                 uint32_t* __restrict__ total_dev) {
+  __shared__ uint32_t chunk_total;
+  uint32_t carry = 0;
+  for (int64_t c = 0; c < nb; c += kScanThreads) {
+    const int64_t i = c + threadIdx.x;
+    uint32_t x = i < nb ? sums[i] : 0u;
+    uint32_t e = block_exclusive(x, &chunk_total);
+    if (i < nb) sums[i] = carry + e;
+    carry += chunk_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+}
+
+__global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_max,
+                                  const uint32_t* n_dev, const uint32_t* __restrict__ sums) {
+  const int64_t n = scan_len(n_max, n_dev);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+  uint32_t v[kScanPerThread];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  __shared__ uint32_t total;
+  uint32_t run = block_exclusive(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)device_sm_count() * 32;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t n_max) { return (size_t)((n_max + kScanTile - 1) / kScanTile) + 1; }
+
+int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max, const uint32_t* n_dev,
+                          uint32_t* block_tmp, uint32_t* total_dev, cudaStream_t st) {
+  if (n_max <= 0) {
+    if (total_dev) VGICP_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st));
+    return VGICP_OK;
+  }
+  const int64_t nb = (n_max + kScanTile - 1) / kScanTile;
+  scan_tile_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n_max, n_dev, block_tmp);
+  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(block_tmp, nb, total_dev);
+  scan_tiles_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n_max, n_dev, block_tmp);
+  VGICP_CUDA_TRY(cudaGetLastError());
+  count_launches(3);
+  return VGICP_OK;
+}
+
+int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t st) {
+  const int64_t n = s->n_total;
+  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_status, 0, sizeof(int32_t), st));
+  if (s->cap_total > 0) {
+    init_slots_kernel<<<grid_for(s->cap_total, kThreads), kThreads, 0, st>>>(s->d_slots,
+                                                                          s->cap_total);
+    count_launches(1);
+  }
+  if (n == 0) {
+    VGICP_CUDA_TRY(cudaMemsetAsync(s->d_num_voxels, 0, sizeof(uint32_t), st));
+    VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vbase, 0, sizeof(uint32_t) * (s->n_maps + 1), st));
+    VGICP_CUDA_TRY(cudaGetLastError());
+    return VGICP_OK;
+  }
+  const float inv_r = (float)(1.0 / s->resolution);
+  const int g = grid_for(n, kThreads);
+  uint32_t* first = s->d_vfill;  // reused: dead after assign, then zeroed
+  insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->n_maps, s->d_slot_base,
+                                        s->d_cap_mask, inv_r, s->resolution, s->max_probe,
+                                        s->d_slots, s->d_pt_slot, s->d_status);
+  first_kernel<<<g, kThreads, 0, st>>>(n, s->d_point_off, s->n_maps, s->d_slots, s->d_pt_slot,
+                                       first);
+  int rc = launch_exclusive_scan(first, s->d_flag, n, nullptr, s->d_scan_tmp, s->d_num_voxels, st);
+  if (rc != VGICP_OK) return rc;
+  assign_kernel<<<g, kThreads, 0, st>>>(n, first, s->d_flag, s->d_pt_slot, s->d_slots,
+                                        s->d_vcount, s->d_vkeys);
+  vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
+                                                            s->d_flag, s->d_num_voxels,
+                                                            s->d_vbase);
+  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
+  rc = launch_exclusive_scan(s->d_vcount, s->d_voff, n, s->d_num_voxels, s->d_scan_tmp, nullptr,
+                             st);
+  if (rc != VGICP_OK) return rc;
+  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_voff, s->d_vfill,
+                                         s->d_plist);
+  finalize_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
+                                          s->d_voff, s->d_plist, s->d_recs);
+  VGICP_CUDA_TRY(cudaGetLastError());
+  count_launches(7);  // insert, first, assign, vbase, scatter, finalize (+ init above: 1)
+  return VGICP_OK;
+}
+
+}  // namespace vgicp

@@ -1,0 +1,123 @@
+// Device-side definitions shared by the build and linearize kernels:
+// the exact voxel key, key packing, the hash, and the table/record layouts.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vgicp {
+
+// ---------------------------------------------------------------------------
+// Layouts in HBM
+// ---------------------------------------------------------------------------
+
+// Hash slot (16 B, 16-B aligned): packed key, then (vid, count).
+//   key   : kEmptyKey or a packed voxel key (< 2^63)
+//   vid   : during the build, the smallest point index (map-local) of the voxel;
+//           after it, the global voxel index
+//   count : number of points in the voxel
+struct __align__(16) Slot {
+  unsigned long long key;
+  uint32_t vid;
+  uint32_t count;
+};
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kKeyBits = 21;
+constexpr int kKeyBias = 1 << (kKeyBits - 1);  // key fields hold k + 2^20
+constexpr int kKeyMin = -kKeyBias;             // valid k: [-2^20, 2^20)
+constexpr int kKeyMax = kKeyBias - 1;
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+// Voxel record: 3 x float4 = 48 B.
+//   r0 = (mu'.x, mu'.y, mu'.z, bits(N)), r1 = (C'xx, C'xy, C'xz, C'yy),
+//   r2 = (C'yz, C'zz, 0, 0)
+constexpr int kRecordF4 = 3;
+
+// Per-map descriptor read by the linearize kernels.
+struct MapDesc {
+  const Slot* slots;   // this map's table (cap slots)
+  const float4* recs;  // global record array (vids are global)
+  uint32_t mask;       // cap - 1
+  int32_t max_probe;
+  float inv_r;         // float32(1 / r)
+  float margin_scale;  // inv_r * 2^-21 (see source_key)
+  double r;
+  const uint32_t* vbase;  // first global voxel index of this map (device)
+};
+
+// Per-factor descriptor: pose in both precisions, map and source index.
+struct PairDesc {
+  float R[9];     // float32(R), row-major
+  float t[3];     // float32(t)
+  float tmax;     // max |t_i| (float32, rounded up)
+  int32_t map;    // index into the MapDesc array
+  int32_t src;    // index into the SrcDesc array
+  int32_t pad;
+  double R64[9];  // binary64 R, row-major
+  double t64[3];
+};
+
+struct SrcDesc {
+  const float* pts;   // n x 3
+  const float* covs;  // n x 6
+  int64_t n;
+};
+
+// Work item: points [begin, end) of pair `pair`.
+struct __align__(16) WorkItem {
+  int32_t pair;
+  int32_t begin;
+  int32_t end;
+  int32_t pad;
+};
+
+// Number of float accumulators per factor: H (21 unique), b (6), err (1),
+// plus the inlier count (carried as a float inside a block, exact below 2^24).
+constexpr int kTerms = 28;
+constexpr int kAcc = kTerms + 1;
+constexpr int kPartialStride = 32;  // doubles per partial record
+
+// ---------------------------------------------------------------------------
+// Voxel key: k = floor(x / r) as if evaluated in binary64.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long pack_key(int kx, int ky, int kz) {
+  return ((unsigned long long)(uint32_t)(kx + kKeyBias) << (2 * kKeyBits)) |
+         ((unsigned long long)(uint32_t)(ky + kKeyBias) << kKeyBits) |
+         (unsigned long long)(uint32_t)(kz + kKeyBias);
+}
+
+__device__ __forceinline__ bool key_in_range(int k) { return k >= kKeyMin && k <= kKeyMax; }
+
+// 32-bit mix of the three key fields; any function works, this one is cheap.
+__device__ __forceinline__ uint32_t hash_key(int kx, int ky, int kz) {
+  uint32_t h = (uint32_t)kx * 0x8DA6B343u + (uint32_t)ky * 0xD8163841u + (uint32_t)kz * 0xCB1AB31Fu;
+  return h ^ (h >> 16);
+}
+
+// Clamp a float to the int range before conversion, so out-of-range values map
+// to out-of-range keys instead of wrapping.
+__device__ __forceinline__ int clamp_to_int(float f) {
+  f = fminf(fmaxf(f, -2147483520.0f), 2147483520.0f);
+  return (int)f;
+}
+
+// Exact key of a float32 coordinate.  Fast path: y = x * float(1/r) in float32;
+// its error is below |y| * 2^-23, so floor(y) equals floor(x / r) unless y is
+// within that distance of an integer; then recompute in binary64.
+__device__ __forceinline__ int axis_key_target(float x, float inv_r, double r) {
+  float y = x * inv_r;
+  float fl = floorf(y);
+  float f = y - fl;
+  float m = fmaf(fabsf(y), 2.384185791015625e-7f /* 2^-22 */, 2.384185791015625e-7f);
+  if (f < m || f > 1.0f - m) {
+    double q = __ddiv_rn((double)x, r);
+    double k = floor(q);
+    k = fmin(fmax(k, -2147483648.0), 2147483647.0);
+    return (int)k;
+  }
+  return clamp_to_int(fl);
+}
+
+}  // namespace vgicp

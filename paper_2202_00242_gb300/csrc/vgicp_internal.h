@@ -1,0 +1,111 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "vgicp.h"
+#include "vgicp_device.cuh"
+
+namespace vgicp {
+
+// ---- error reporting -------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int check_cuda(cudaError_t e, const char* what);
+#define VGICP_CUDA_TRY(call)                                   \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return check_cuda(e__, #call);     \
+  } while (0)
+
+// ---- map storage -----------------------------------------------------------
+// One build batch: n_maps maps built from concatenated clouds.  All device
+// buffers are sized at creation so that rebuilds allocate nothing.
+struct MapSet {
+  int refcount = 0;
+  int device = 0;
+  int32_t n_maps = 0;
+  double resolution = 0.0;
+  int32_t max_probe = 64;
+  int64_t n_total = 0;    // points over all maps
+  int64_t cap_total = 0;  // slots over all maps
+  std::vector<int64_t> point_off;  // n_maps + 1
+  std::vector<int64_t> slot_base;  // n_maps
+  std::vector<uint32_t> cap;       // n_maps
+  // device: per-map metadata
+  int64_t* d_point_off = nullptr;  // n_maps + 1
+  int64_t* d_slot_base = nullptr;  // n_maps
+  uint32_t* d_cap_mask = nullptr;  // n_maps
+  uint32_t* d_vbase = nullptr;     // n_maps + 1: first global voxel index of each map
+  // device: the maps
+  Slot* d_slots = nullptr;                  // cap_total
+  float4* d_recs = nullptr;                 // n_total * 3 (V <= n_total)
+  unsigned long long* d_vkeys = nullptr;    // n_total (packed keys by voxel)
+  int32_t* d_status = nullptr;              // 1
+  // device: build scratch (kept for rebuilds)
+  uint32_t* d_pt_slot = nullptr;  // n_total
+  uint32_t* d_flag = nullptr;     // n_total: first-point flags, then voxel ids
+  uint32_t* d_vcount = nullptr;   // n_total
+  uint32_t* d_voff = nullptr;     // n_total
+  uint32_t* d_vfill = nullptr;    // n_total
+  uint32_t* d_plist = nullptr;    // n_total
+  uint32_t* d_scan_tmp = nullptr; // scan block sums
+  uint32_t* d_num_voxels = nullptr;  // 1 (total V)
+  size_t scan_tmp_elems = 0;
+  void* d_block = nullptr;        // single allocation holding everything above
+};
+
+}  // namespace vgicp
+
+struct vgicp_map {
+  vgicp::MapSet* set;
+  int32_t index;
+};
+
+namespace vgicp {
+
+// ---- kernels (vgicp_build.cu) ---------------------------------------------
+int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t st);
+
+// exclusive scan of n_max uint32 (elements at or beyond *n_dev, if given, count
+// as 0); writes the total to *total_dev if non-null.
+int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max,
+                          const uint32_t* n_dev, uint32_t* block_tmp, uint32_t* total_dev,
+                          cudaStream_t st);
+size_t scan_tmp_elems(int64_t n_max);
+
+// ---- kernels (vgicp_linearize.cu) ----------------------------------------
+struct LinLaunch {
+  const WorkItem* items;     // null: uniform tiles of pair 0 (single factor)
+  int32_t n_items;
+  int32_t tile;              // uniform-tile mode
+  const PairDesc* pairs;     // null: use `single`
+  const MapDesc* maps;       // null: use `single_map`
+  const SrcDesc* srcs;       // null: use `single_src`
+  PairDesc single;
+  MapDesc single_map;
+  SrcDesc single_src;
+  double* partials;          // n_items x kPartialStride
+  int32_t* corr_out;
+  int32_t* qkey_out;
+  int32_t neighbours;
+  int32_t grid;
+  int32_t block;
+  cudaEvent_t ev_start;      // optional, recorded around the kernel
+  cudaEvent_t ev_stop;
+};
+int launch_linearize(const LinLaunch& L, cudaStream_t st);
+
+// Sum the partials of each pair's items [item_off[p], item_off[p+1]) in order.
+int launch_reduce(const double* partials, const int32_t* item_off, int32_t n_items_single,
+                  int64_t n_pairs, double* out, int64_t* inliers, cudaStream_t st);
+
+int device_sm_count();
+
+// Count of kernels launched by the library (vgicp_launch_count).
+void count_launches(int n);
+
+}  // namespace vgicp

@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded inputs.
+
+Bars (arXiv 2202.00242 Sec. III-A quantities):
+  * voxel keys, per-voxel counts and voxel order: bit-exact; voxel means and
+    covariances: bit-exact with the binary64 definition rounded to float32;
+  * per-point correspondences (voxel index) and keys of T mu: bit-exact; the
+    number of points within 1e-5 m of a voxel face is reported;
+  * H: relative Frobenius error <= 1e-4; b: error <= 1e-4 relative to
+    max(|b|, sqrt(err |H|_F)); err: relative error <= 1e-4; inliers exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2202_00242_gb300 import api, synth
+from paper_2202_00242_gb300._lib import VGICPError
+
+import cases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_00242_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check_factor(out, inl, ref, what=""):
+    H, b, err = api.unpack(out.cpu().double())
+    H, b, err = H.numpy(), b.numpy(), float(err)
+    assert int(inl) == ref.inliers, what
+    eH = cases.rel_fro(H, ref.H)
+    eb = cases.b_error(b, ref.b, ref.err, ref.H)
+    ee = abs(err - ref.err) / max(abs(ref.err), 1e-300)
+    assert eH <= TOL and eb <= TOL and ee <= TOL, (what, eH, eb, ee)
+    assert np.array_equal(H, H.T)
+    return eH, eb, ee
+
+
+@pytest.mark.parametrize("r", [0.5, 0.25, 1.0, 0.3])
+def test_voxelmap_bit_exact(dev, r):
+    tp, tc, _, _, _, _ = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    vm.status()
+    ex = vm.export()
+    ref = oracle.build_voxelmap(tp, tc, r)
+    assert np.array_equal(ex["keys"], ref.keys)
+    assert np.array_equal(ex["counts"], ref.counts)
+    assert np.array_equal(ex["means"], ref.means.astype(np.float32))
+    assert np.array_equal(ex["covs"], ref.covs.astype(np.float32))
+
+
+def test_voxelmap_points_on_faces(dev):
+    # coordinates on exact multiples of r and just below: floor semantics at faces
+    r = 0.5
+    g = np.arange(-8, 8, dtype=np.float64) * r
+    pts = np.stack(np.meshgrid(g, g, g[:4]), -1).reshape(-1, 3)
+    pts = np.concatenate([pts, np.nextafter(pts.astype(np.float32), -np.inf)]).astype(np.float32)
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (pts.shape[0], 1))
+    vm = api.VoxelMap.build(cu(pts), cu(covs), r)
+    vm.status()
+    ex = vm.export()
+    ref = oracle.build_voxelmap(pts, covs, r)
+    assert np.array_equal(ex["keys"], ref.keys)
+    assert np.array_equal(ex["counts"], ref.counts)
+    assert np.array_equal(ex["means"], ref.means.astype(np.float32))
+
+
+@pytest.mark.parametrize("which", ["planted", "identity", "perturbed"])
+def test_linearize_room_matches_oracle(dev, which):
+    tp, tc, sp, sc, T_true, r = cases.room()
+    T = {"planted": T_true, "identity": np.eye(4),
+         "perturbed": synth.perturb_pose(np.random.default_rng(3), T_true, 0.05, 1.0)}[which]
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    lin = api.linearize(vm, cu(sp), cu(sc), T, corr=True, qkeys=True)
+    ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, debug=True)
+    assert np.array_equal(lin.qkeys.cpu().numpy().astype(np.int64), ref.qkeys)
+    assert np.array_equal(lin.corr.cpu().numpy().astype(np.int64), ref.corr)
+    check_factor(lin.out, lin.inliers, ref, which)
+    print(f"near-face points (<1e-5 m): {cases.near_face_count(sp, T, r)} of {sp.shape[0]}")
+
+
+@pytest.mark.parametrize("n", [1, 31, 255, 256, 257, 1000, 8191])
+@pytest.mark.parametrize("tile", [256, 1024, 0])
+def test_ragged_sizes_and_tiles(dev, n, tile):
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    lin = api.linearize(vm, cu(sp[:n]), cu(sc[:n]), T, tile=tile)
+    ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp[:n], sc[:n], T)
+    if ref.inliers == 0:
+        assert int(lin.inliers) == 0
+        return
+    check_factor(lin.out, lin.inliers, ref, f"n={n} tile={tile}")
+
+
+def test_empty_inputs(dev):
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    e = api.linearize(vm, cu(sp[:0]), cu(sc[:0]), T)
+    assert int(e.inliers) == 0 and not e.out.any()
+    empty = api.VoxelMap.build(cu(tp[:0]), cu(tc[:0]), r)
+    empty.status()
+    assert empty.info()[0] == 0
+    m = api.linearize(empty, cu(sp), cu(sc), T)
+    assert int(m.inliers) == 0 and not m.out.any()
+    far = T.copy()
+    far[:3, 3] += 5000.0
+    f = api.linearize(vm, cu(sp), cu(sc), far)
+    assert int(f.inliers) == 0 and not f.out.any()
+
+
+def test_batched_equals_single_bitwise(dev):
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    poses = [T, np.eye(4), synth.perturb_pose(np.random.default_rng(1), T, 0.1, 2.0)]
+    srcs = [(cu(sp), cu(sc)), (cu(sp[:5000]), cu(sc[:5000]))]
+    pairs = np.array([[0, 0], [0, 1], [0, 0]])
+    bat = api.linearize_batched([vm], srcs, pairs, np.stack(poses), tile=1024)
+    for p in range(3):
+        s = srcs[pairs[p, 1]]
+        one = api.linearize(vm, s[0], s[1], poses[p], tile=1024)
+        assert torch.equal(bat.out[p], one.out), p
+        assert int(bat.inliers[p]) == int(one.inliers)
+
+
+@pytest.mark.parametrize("r", [0.25, 1.0])
+def test_corridor_window_batched(dev, r):
+    w = cases.workload_with_knn_covs("corridor", resolution=r, perturb=(0.05, 1.0))
+    K = len(w.clouds.offsets) - 2
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts[: w.clouds.offsets[K]], covs[: w.clouds.offsets[K]],
+                               w.clouds.offsets[: K + 1], r)
+    maps[0].status()
+    sp, sc = w.clouds.cloud(K)
+    src = [(cu(sp), cu(sc))]
+    pairs = np.stack([np.arange(K), np.zeros(K, np.int64)], 1)
+    bat = api.linearize_batched(maps, src, pairs, w.poses)
+    for k in range(K):
+        tp, tc = w.clouds.cloud(k)
+        ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, w.poses[k], nthreads=0)
+        check_factor(bat.out[k], bat.inliers[k], ref, f"keyframe {k}")
+
+
+def test_outdoor_submaps_batched(dev):
+    w = cases.workload_with_knn_covs("outdoor", seed=33, n_submaps=10, neighbours=3)
+    C = len(w.clouds.offsets) - 1
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    srcs = [(pts[w.clouds.offsets[c]:w.clouds.offsets[c + 1]],
+             covs[w.clouds.offsets[c]:w.clouds.offsets[c + 1]]) for c in range(C)]
+    bat = api.linearize_batched(maps, srcs, w.pairs, w.poses, tile=4096)
+    omaps = {}
+    for p, (j, i) in enumerate(w.pairs):
+        if j not in omaps:
+            tp, tc = w.clouds.cloud(j)
+            omaps[j] = oracle.build_voxelmap(tp, tc, w.resolution)
+        sp, sc = w.clouds.cloud(i)
+        ref = oracle.linearize(omaps[j], sp, sc, w.poses[p], nthreads=0)
+        check_factor(bat.out[p], bat.inliers[p], ref, f"pair {p}")
+
+
+@pytest.mark.parametrize("mode", ["single", "batched"])
+def test_27_neighbours_match_oracle(dev, mode):
+    tp, tc, sp, sc, T, r = cases.room(seed=4, n_target=4096, n_source=3000)
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, neighbours=27,
+                           debug=True)
+    if mode == "single":
+        lin = api.linearize(vm, cu(sp), cu(sc), T, neighbours=27, corr=True)
+        assert np.array_equal(lin.corr.cpu().numpy().astype(np.int64), ref.corr)
+        out, inl = lin.out, lin.inliers
+    else:
+        bat = api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 0]], T[None], neighbours=27,
+                                    tile=512)
+        out, inl = bat.out[0], bat.inliers[0]
+    check_factor(out, inl, ref, mode)
+
+
+def test_repeated_linearizations_identical(dev):
+    w = cases.workload_with_knn_covs("corridor", resolution=0.25, perturb=(0.05, 1.0))
+    K = len(w.clouds.offsets) - 2
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts[: w.clouds.offsets[K]], covs[: w.clouds.offsets[K]],
+                               w.clouds.offsets[: K + 1], 0.25)
+    sp, sc = w.clouds.cloud(K)
+    src = [(cu(sp), cu(sc))]
+    pairs = np.stack([np.arange(K), np.zeros(K, np.int64)], 1)
+    first = api.linearize_batched(maps, src, pairs, w.poses).out.clone()
+    for _ in range(100):
+        again = api.linearize_batched(maps, src, pairs, w.poses).out
+        assert torch.equal(first, again)
+
+
+def test_rebuild_matches_fresh_build(dev):
+    w = cases.workload_with_knn_covs("corridor", resolution=0.25, perturb=(0.05, 1.0))
+    K = len(w.clouds.offsets) - 2
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    off = w.clouds.offsets[: K + 1]
+    maps = api.build_voxelmaps(pts[: off[-1]], covs[: off[-1]], off, 0.25)
+    # rebuild from shuffled-within-cloud data, then back to the original
+    perm = np.concatenate([np.random.default_rng(0).permutation(np.arange(off[c], off[c + 1]))
+                           for c in range(K)])
+    api.rebuild_voxelmaps(maps, pts[perm].contiguous(), covs[perm].contiguous())
+    maps[0].status()
+    api.rebuild_voxelmaps(maps, pts[: off[-1]], covs[: off[-1]])
+    fresh = api.build_voxelmaps(pts[: off[-1]], covs[: off[-1]], off, 0.25)
+    for a, b in zip(maps, fresh):
+        ea, eb = a.export(), b.export()
+        for k in ea:
+            assert np.array_equal(ea[k], eb[k])
+
+
+def test_build_error_paths_leave_context_usable(dev):
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(-100, 100, size=(4096, 3)).astype(np.float32)
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (4096, 1))
+    full = api.VoxelMap.build(cu(pts), cu(covs), 0.01, max_probe=1, capacity_factor=1)
+    with pytest.raises(VGICPError) as e:
+        full.status()
+    assert e.value.code == -3
+    far = pts.copy()
+    far[7] = [3.0e7, 0.0, 0.0]
+    bad = api.VoxelMap.build(cu(far), cu(covs), 0.5)
+    with pytest.raises(VGICPError) as e:
+        bad.status()
+    assert e.value.code == -4
+    nan = pts.copy()
+    nan[3, 1] = np.nan
+    badn = api.VoxelMap.build(cu(nan), cu(covs), 0.5)
+    with pytest.raises(VGICPError) as e:
+        badn.status()
+    assert e.value.code == -4
+    # the context still works
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    vm.status()
+    lin = api.linearize(vm, cu(sp), cu(sc), T)
+    ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T)
+    check_factor(lin.out, lin.inliers, ref)
+
+
+def test_pose_validation(dev):
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    bad = T.copy()
+    bad[0, 3] = np.nan
+    with pytest.raises(VGICPError) as e:
+        api.linearize(vm, cu(sp), cu(sc), bad)
+    assert e.value.code == -1
+    scaled = T.copy()
+    scaled[:3, :3] *= 1.1
+    with pytest.raises(VGICPError):
+        api.linearize(vm, cu(sp), cu(sc), scaled)
+    with pytest.raises(VGICPError):
+        api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 1]], T[None])
