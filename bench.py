@@ -47,6 +47,11 @@ def parse_args(argv=None):
     ap.add_argument("--neighbours-per-submap", type=int, default=10)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="1-neighbour kernel: 0 auto, 1 per-point, 2 shared-memory staged")
+    ap.add_argument("--sources", choices=["maps", "clouds"], default="maps",
+                    help="maps: each submap's own (voxel-grouped) cloud is the source of its "
+                         "factors; clouds: the caller's arrays as given")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle baseline sample")
@@ -137,12 +142,14 @@ def workload_config(w, args, extra=None):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """Samples SM clocks and throttle reasons with nvidia-smi every 100 ms."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_id=None):
-        self.gpu_id = gpu_id
+    def __init__(self, uuid=None):
+        self.uuid = (uuid or "").lower().replace("gpu-", "")
         self.proc = None
         self.path = None
 
@@ -152,8 +159,6 @@ class ClockSampler:
             os.close(fd)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                    "-lms", "100"]
-            if self.gpu_id is not None:
-                cmd += ["-i", str(self.gpu_id)]
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
                                          stderr=subprocess.DEVNULL)
         except Exception:
@@ -172,6 +177,8 @@ class ClockSampler:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
+            if self.uuid and self.uuid not in parts[0].lower():
+                continue
             try:
                 rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
@@ -179,8 +186,8 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        reasons = sorted({self.REASONS[i] for _, _, r in rows for i in range(4)
+                          if r[i].lower() == "active"})
         sm = [r[0] for r in rows]
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
                 "reasons": reasons, "samples": len(rows)}
@@ -250,7 +257,10 @@ def run_ours(args):
     covs = torch.from_numpy(w.clouds.covs).to(dev)
     maps = api.build_voxelmaps(pts, covs, off, w.resolution)
     maps[0].status()
-    srcs = [(pts[off[c]:off[c + 1]], covs[off[c]:off[c + 1]]) for c in range(C)]
+    if args.sources == "maps":
+        srcs = maps
+    else:
+        srcs = [(pts[off[c]:off[c + 1]], covs[off[c]:off[c + 1]]) for c in range(C)]
     P = w.pairs.shape[0]
     out = torch.empty((P, api.RESULT_SIZE), dtype=torch.float64, device=dev)
     inl = torch.empty(P, dtype=torch.int64, device=dev)
@@ -259,10 +269,8 @@ def run_ours(args):
 
     def step(ev=None):
         api.rebuild_voxelmaps(maps, pts, covs)
-        kw = {}
-        if ev is not None:
-            kw = {"events": ev}
-        linearize_batched_timed(api, maps, srcs, w.pairs, w.poses, out, inl, args, **kw)
+        api.linearize_batched(maps, srcs, w.pairs, w.poses, tile=args.tile, grid=args.grid,
+                              variant=args.variant, out=out, inliers=inl, events=ev)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -353,10 +361,12 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded city-loop submaps; no dataset available)",
             "config": workload_config(w, args, {"parallelism": f"independent factor sets x{world}",
-                                                "tile": args.tile or 8192}),
+                                                "sources": args.sources,
+                                                "kernel_variant": args.variant or "auto",
+                                                "item_points": args.tile or 16384}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "linearize_kernel<1>", "kernel_ms": kernel_ms,
+                         "kernel": "linearize (1-neighbour)", "kernel_ms": kernel_ms,
                          "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pts,
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"},
             "e2e": {"value": e2e_value, "unit": "source pts/s", "h2d_bytes_per_step": h2d,
@@ -369,26 +379,6 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def linearize_batched_timed(api, maps, srcs, pairs, poses, out, inl, args, events=None):
-    import ctypes
-
-    from paper_2202_00242_gb300 import _lib
-    from paper_2202_00242_gb300._lib import LinOpts, check
-    pairs = np.ascontiguousarray(pairs, dtype=np.int32)
-    poses = np.ascontiguousarray(poses, dtype=np.float64)
-    clouds = api.make_clouds(srcs)
-    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
-    ev0 = ctypes.c_void_p(events[0].cuda_event) if events is not None else None
-    ev1 = ctypes.c_void_p(events[1].cuda_event) if events is not None else None
-    opts = LinOpts(1, int(args.tile), int(args.grid), 0, None, None, ev0, ev1)
-    import torch
-    check(_lib.load().vgicp_linearize_batched(
-        arr, len(maps), clouds, len(srcs), pairs.ctypes.data_as(ctypes.c_void_p), pairs.shape[0],
-        poses.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(out.data_ptr()),
-        ctypes.c_void_p(inl.data_ptr()), ctypes.byref(opts),
-        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -133,7 +133,8 @@ typedef struct {
                          one independent term each; 0 = 1 */
   int32_t tile;       /* source points per work item; 0 = automatic */
   int32_t grid;       /* CTAs of the persistent launch; 0 = automatic */
-  int32_t reserved;
+  int32_t variant;    /* 1-neighbour kernel: 0 = automatic, 1 = one point per thread,
+                         2 = shared-memory staged (bulk asynchronous copies) */
   int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
                          point's own voxel (first-appearance numbering) or -1 */
   int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
@@ -150,11 +151,18 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
                     int64_t n_src, const double* T_target_source, double* out, int64_t* inliers,
                     const vgicp_lin_opts* opts, vgicp_stream_t stream);
 
-/* A source cloud for batched calls (device pointers). */
+/* A source cloud for batched calls (device pointers), or a voxel map whose own
+ * cloud is the source: when `map` is non-null, points/covs/n are ignored and the
+ * map's cloud is read in the voxel-grouped order its build produced (points of
+ * one voxel contiguous), which makes neighbouring source points look up
+ * neighbouring target voxels.  The sum over points does not depend on the
+ * order; the float32 rounding does, within the library's tolerance.  Results
+ * are undefined if that map's build reported an error. */
 typedef struct {
   const float* points; /* n x 3 */
   const float* covs;   /* n x 6 */
   int64_t n;
+  const vgicp_map* map;
 } vgicp_cloud;
 
 /* Linearize n_pairs independent factors in one persistent launch (Sec. III-F:

@@ -21,12 +21,12 @@ class MapOpts(ctypes.Structure):
 
 
 class LinOpts(ctypes.Structure):
-    _fields_ = [("neighbours", i32), ("tile", i32), ("grid", i32), ("reserved", i32),
+    _fields_ = [("neighbours", i32), ("tile", i32), ("grid", i32), ("variant", i32),
                 ("corr_out", P), ("qkey_out", P), ("kernel_start", P), ("kernel_stop", P)]
 
 
 class Cloud(ctypes.Structure):
-    _fields_ = [("points", P), ("covs", P), ("n", i64)]
+    _fields_ = [("points", P), ("covs", P), ("n", i64), ("map", P)]
 
 
 # name -> (restype, argtypes); mirrors include/vgicp.h

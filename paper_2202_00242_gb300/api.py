@@ -168,7 +168,7 @@ def unpack(out):
 
 
 def linearize(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T, neighbours=1, tile=0,
-              grid=0, corr=False, qkeys=False, out=None, inliers=None,
+              grid=0, corr=False, qkeys=False, out=None, inliers=None, variant=0,
               stream=None) -> Linearization:
     """Linearize one factor at T = T_target_source (Eqs. 2-3 of arXiv 2202.00242)."""
     _check_cloud(points, covs, "source")
@@ -181,9 +181,9 @@ def linearize(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T, neigh
         inliers = torch.empty((), dtype=torch.int64, device=dev)
     c = torch.empty(n, dtype=torch.int32, device=dev) if corr else None
     q = torch.empty((n, 3), dtype=torch.int32, device=dev) if qkeys else None
-    opts = LinOpts(int(neighbours), int(tile), int(grid), 0,
+    opts = LinOpts(int(neighbours), int(tile), int(grid), int(variant),
                    ctypes.c_void_p(c.data_ptr()) if c is not None else None,
-                   ctypes.c_void_p(q.data_ptr()) if q is not None else None)
+                   ctypes.c_void_p(q.data_ptr()) if q is not None else None, None, None)
     check(_lib.load().vgicp_linearize(vmap.handle, ctypes.c_void_p(points.data_ptr()),
                                       ctypes.c_void_p(covs.data_ptr()), n,
                                       T.ctypes.data_as(ctypes.c_void_p),
@@ -194,29 +194,39 @@ def linearize(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T, neigh
 
 
 def make_clouds(sources) -> tuple:
-    """ctypes array of vgicp_cloud from a list of (points, covs) tensors."""
+    """ctypes array of vgicp_cloud from a list whose entries are (points, covs)
+    tensors or VoxelMap objects (the map's own cloud, in voxel-grouped order)."""
     arr = (Cloud * len(sources))()
-    for i, (p, c) in enumerate(sources):
-        _check_cloud(p, c, f"source {i}")
-        arr[i] = Cloud(p.data_ptr(), c.data_ptr(), p.shape[0])
+    for i, src in enumerate(sources):
+        if isinstance(src, VoxelMap):
+            arr[i] = Cloud(None, None, 0, src.handle.value)
+        else:
+            p, c = src
+            _check_cloud(p, c, f"source {i}")
+            arr[i] = Cloud(p.data_ptr(), c.data_ptr(), p.shape[0], None)
     return arr
 
 
 def linearize_batched(maps: list[VoxelMap], sources, pairs, poses, neighbours=1, tile=0, grid=0,
-                      out=None, inliers=None, stream=None) -> Linearization:
+                      out=None, inliers=None, variant=0, events=None,
+                      stream=None) -> Linearization:
     """Linearize many factors in one persistent launch.  sources: list of (points,
-    covs); pairs: (P, 2) int (map index, source index); poses: (P, 4, 4)."""
+    covs) or VoxelMap (its own cloud); pairs: (P, 2) int (map index, source
+    index); poses: (P, 4, 4).  events: optional (start, stop) torch.cuda.Event
+    recorded around the linearize kernel."""
     pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     P = pairs.shape[0]
     poses = _pose_array(poses, P)
-    dev = sources[0][0].device
+    dev = torch.device("cuda", torch.cuda.current_device())
     if out is None:
         out = torch.empty((P, RESULT_SIZE), dtype=torch.float64, device=dev)
     if inliers is None:
         inliers = torch.empty(P, dtype=torch.int64, device=dev)
     clouds = make_clouds(sources)
     arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
-    opts = LinOpts(int(neighbours), int(tile), int(grid), 0, None, None)
+    ev0 = ctypes.c_void_p(events[0].cuda_event) if events is not None else None
+    ev1 = ctypes.c_void_p(events[1].cuda_event) if events is not None else None
+    opts = LinOpts(int(neighbours), int(tile), int(grid), int(variant), None, None, ev0, ev1)
     check(_lib.load().vgicp_linearize_batched(arr, len(maps), clouds, len(sources),
                                               pairs.ctypes.data_as(ctypes.c_void_p), P,
                                               poses.ctypes.data_as(ctypes.c_void_p),

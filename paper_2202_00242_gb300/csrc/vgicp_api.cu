@@ -67,9 +67,9 @@ PairDesc make_pair_desc(const double* T, int32_t map, int32_t src) {
 MapDesc make_map_desc(const vgicp_map* m) {
   const MapSet* s = m->set;
   MapDesc d;
-  d.slots = s->d_slots + s->slot_base[m->index];
-  d.recs = s->d_recs;
-  d.mask = s->cap[m->index] - 1u;
+  std::memset(&d, 0, sizeof(d));
+  d.vslots = s->d_vslots + s->vslot_base[m->index];
+  d.vmask = s->d_vmask + m->index;
   d.max_probe = s->max_probe;
   d.inv_r = (float)(1.0 / s->resolution);
   d.margin_scale = d.inv_r * 4.76837158203125e-7f;  // 2^-21
@@ -95,6 +95,7 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   if (!(resolution > 0.0) || !std::isfinite(resolution))
     return set_error(VGICP_ERR_INVALID_ARG, "resolution must be positive and finite");
   if (n_maps <= 0 || !offsets) return set_error(VGICP_ERR_INVALID_ARG, "n_maps must be >= 1");
+  if (n_maps > 65535) return set_error(VGICP_ERR_INVALID_ARG, "at most 65535 maps per batch");
   if (offsets[0] != 0) return set_error(VGICP_ERR_INVALID_ARG, "offsets[0] must be 0");
   for (int32_t m = 0; m < n_maps; ++m)
     if (offsets[m + 1] < offsets[m])
@@ -111,16 +112,21 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->n_total = offsets[n_maps];
   s->slot_base.resize(n_maps);
   s->cap.resize(n_maps);
-  int64_t cap_total = 0;
+  s->vslot_base.resize(n_maps);
+  int64_t cap_total = 0, vcap_total = 0;
   for (int32_t m = 0; m < n_maps; ++m) {
     int64_t n = offsets[m + 1] - offsets[m];
     uint32_t c = next_pow2((uint64_t)std::max<int64_t>(n, 1) * (uint64_t)cf);
     s->cap[m] = c;
     s->slot_base[m] = cap_total;
     cap_total += c;
+    s->vslot_base[m] = vcap_total;
+    vcap_total += next_pow2((uint64_t)std::max<int64_t>(n, 8) * 2u);
   }
   s->cap_total = cap_total;
-  if (s->n_total >= (int64_t)0xFFFFFFFFll || cap_total >= (int64_t)0xFFFFFFFFll) {
+  s->vcap_total = vcap_total;
+  if (s->n_total >= (int64_t)0xFFFFFFFFll || cap_total >= (int64_t)0xFFFFFFFFll ||
+      vcap_total >= (int64_t)0xFFFFFFFFll) {
     delete s;
     return set_error(VGICP_ERR_INVALID_ARG, "more than 2^32-1 points or slots in one batch");
   }
@@ -135,19 +141,34 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   };
   const size_t o_point_off = take(sizeof(int64_t) * (n_maps + 1));
   const size_t o_slot_base = take(sizeof(int64_t) * n_maps);
+  const size_t o_vslot_base = take(sizeof(int64_t) * n_maps);
   const size_t o_cap_mask = take(sizeof(uint32_t) * n_maps);
   const size_t o_vbase = take(sizeof(uint32_t) * (n_maps + 1));
   const size_t o_slots = take(sizeof(Slot) * cap_total);
+  const size_t o_vslots = take(sizeof(VSlot) * vcap_total);
+  const size_t o_vmask = take(sizeof(uint32_t) * n_maps);
   const size_t o_recs = take(sizeof(float4) * kRecordF4 * n);
   const size_t o_vkeys = take(sizeof(unsigned long long) * n);
   const size_t o_status = take(sizeof(int32_t));
   const size_t o_num_vox = take(sizeof(uint32_t));
+  const size_t o_num_valid = take(sizeof(uint32_t));
   const size_t o_pt_slot = take(sizeof(uint32_t) * n);
   const size_t o_flag = take(sizeof(uint32_t) * n);
   const size_t o_vcount = take(sizeof(uint32_t) * n);
   const size_t o_voff = take(sizeof(uint32_t) * n);
   const size_t o_vfill = take(sizeof(uint32_t) * n);
   const size_t o_plist = take(sizeof(uint32_t) * n);
+  std::vector<int2> chunks;
+  for (int32_t m = 0; m < n_maps; ++m) {
+    const int64_t nm = offsets[m + 1] - offsets[m];
+    for (int64_t c = 0; c * kMortonChunk < std::max<int64_t>(nm, 1); ++c)
+      chunks.push_back(make_int2(m, (int)c));
+  }
+  s->n_chunks = (int32_t)chunks.size();
+  const size_t o_chunks = take(sizeof(int2) * chunks.size());
+  const size_t o_goff = take(sizeof(uint32_t) * n);
+  const size_t o_gpts = take(sizeof(float) * 3 * n);
+  const size_t o_gcovs = take(sizeof(float) * 6 * n);
   const size_t o_scan = take(sizeof(uint32_t) * s->scan_tmp_elems);
   cudaError_t e = cudaMalloc(&s->d_block, off);
   if (e != cudaSuccess) {
@@ -159,19 +180,27 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   char* b = static_cast<char*>(s->d_block);
   s->d_point_off = reinterpret_cast<int64_t*>(b + o_point_off);
   s->d_slot_base = reinterpret_cast<int64_t*>(b + o_slot_base);
+  s->d_vslot_base = reinterpret_cast<int64_t*>(b + o_vslot_base);
   s->d_cap_mask = reinterpret_cast<uint32_t*>(b + o_cap_mask);
   s->d_vbase = reinterpret_cast<uint32_t*>(b + o_vbase);
   s->d_slots = reinterpret_cast<Slot*>(b + o_slots);
+  s->d_vslots = reinterpret_cast<VSlot*>(b + o_vslots);
+  s->d_vmask = reinterpret_cast<uint32_t*>(b + o_vmask);
   s->d_recs = reinterpret_cast<float4*>(b + o_recs);
   s->d_vkeys = reinterpret_cast<unsigned long long*>(b + o_vkeys);
   s->d_status = reinterpret_cast<int32_t*>(b + o_status);
   s->d_num_voxels = reinterpret_cast<uint32_t*>(b + o_num_vox);
+  s->d_num_valid = reinterpret_cast<uint32_t*>(b + o_num_valid);
   s->d_pt_slot = reinterpret_cast<uint32_t*>(b + o_pt_slot);
   s->d_flag = reinterpret_cast<uint32_t*>(b + o_flag);
   s->d_vcount = reinterpret_cast<uint32_t*>(b + o_vcount);
   s->d_voff = reinterpret_cast<uint32_t*>(b + o_voff);
   s->d_vfill = reinterpret_cast<uint32_t*>(b + o_vfill);
   s->d_plist = reinterpret_cast<uint32_t*>(b + o_plist);
+  s->d_gpts = reinterpret_cast<float*>(b + o_gpts);
+  s->d_goff = reinterpret_cast<uint32_t*>(b + o_goff);
+  s->d_chunks = reinterpret_cast<int2*>(b + o_chunks);
+  s->d_gcovs = reinterpret_cast<float*>(b + o_gcovs);
   s->d_scan_tmp = reinterpret_cast<uint32_t*>(b + o_scan);
   cudaGetDevice(&s->device);
   std::vector<uint32_t> mask(n_maps);
@@ -183,7 +212,13 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
     e = cudaMemcpy(s->d_slot_base, s->slot_base.data(), sizeof(int64_t) * n_maps,
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_vslot_base, s->vslot_base.data(), sizeof(int64_t) * n_maps,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
     e = cudaMemcpy(s->d_cap_mask, mask.data(), sizeof(uint32_t) * n_maps, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_chunks, chunks.data(), sizeof(int2) * chunks.size(),
+                   cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(s->d_block);
     delete s;
@@ -388,42 +423,45 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-  int tile = opts && opts->tile > 0 ? opts->tile : 0;
-  if (tile == 0) {
-    const int64_t target_items = (int64_t)device_sm_count() * 2;
+  int item = opts && opts->tile > 0 ? opts->tile : 0;
+  if (item == 0) {
+    // spread one factor over the persistent grid, 256..16K points per item
+    const int64_t target_items =
+        linearize_grid(neighbours, opts && opts->variant ? opts->variant : default_variant());
     int64_t t = (n_src + target_items - 1) / std::max<int64_t>(target_items, 1);
-    t = std::max<int64_t>(256, std::min<int64_t>(8192, (t + 255) / 256 * 256));
-    tile = (int)t;
+    t = std::max<int64_t>(256, std::min<int64_t>(default_item_size(), (t + 255) / 256 * 256));
+    item = (int)t;
   }
-  const int32_t n_items = (int32_t)((n_src + tile - 1) / tile);
+  const int32_t n_items = (int32_t)((n_src + item - 1) / item);
 
   LinLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.items = nullptr;
   L.n_items = n_items;
-  L.tile = tile;
+  L.item_size = item;
   L.single = make_pair_desc(T_target_source, 0, 0);
   L.single_map = make_map_desc(map);
   L.single_src = SrcDesc{src_points, src_covs, n_src};
   L.corr_out = opts ? opts->corr_out : nullptr;
   L.qkey_out = opts ? opts->qkey_out : nullptr;
   L.neighbours = neighbours;
+  L.variant = opts ? opts->variant : 0;
   L.grid = opts ? opts->grid : 0;
-  L.block = 0;
   L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
   L.ev_stop = opts ? static_cast<cudaEvent_t>(opts->kernel_stop) : nullptr;
-  double* partials = nullptr;
-  if (n_items > 0) {
-    VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&partials),
-                                   sizeof(double) * kPartialStride * n_items, st));
-  }
-  L.partials = partials;
-  rc = launch_linearize(L, st);
-  if (rc == VGICP_OK) rc = launch_reduce(partials, nullptr, n_items, 1, out, inliers, st);
-  if (partials) {
-    cudaError_t e = cudaFreeAsync(partials, st);
-    if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");
-  }
+  // scratch: partials (n_items x 32 doubles) followed by the status word
+  char* scratch = nullptr;
+  const size_t part_bytes = sizeof(double) * kPartialStride * std::max<int32_t>(n_items, 1);
+  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), part_bytes + 256, st));
+  L.partials = reinterpret_cast<double*>(scratch);
+  L.status = reinterpret_cast<int32_t*>(scratch + part_bytes);
+  cudaError_t e = cudaMemsetAsync(L.status, 0, sizeof(int32_t), st);
+  rc = e == cudaSuccess ? VGICP_OK : check_cuda(e, "cudaMemsetAsync");
+  if (rc == VGICP_OK) rc = launch_linearize(L, st);
+  if (rc == VGICP_OK)
+    rc = launch_reduce(L.partials, nullptr, n_items, 1, L.status, out, inliers, st);
+  e = cudaFreeAsync(scratch, st);
+  if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");
   return rc;
 }
 
@@ -442,18 +480,30 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
+  if (opts && (opts->variant < 0 || opts->variant > 2))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
+  // resolve sources: user clouds, or a map's own voxel-grouped cloud
+  std::vector<SrcDesc> sd((size_t)n_sources);
   for (int32_t c = 0; c < n_sources; ++c) {
-    int rc = check_cloud(sources[c].points, sources[c].covs, sources[c].n, "source cloud");
-    if (rc) return rc;
+    if (sources[c].map) {
+      const vgicp_map* m = sources[c].map;
+      const MapSet* ms = m->set;
+      const int64_t a = ms->point_off[m->index], b = ms->point_off[m->index + 1];
+      sd[(size_t)c] = SrcDesc{ms->d_gpts + 3 * a, ms->d_gcovs + 6 * a, b - a};
+    } else {
+      int rc = check_cloud(sources[c].points, sources[c].covs, sources[c].n, "source cloud");
+      if (rc) return rc;
+      sd[(size_t)c] = SrcDesc{sources[c].points, sources[c].covs, sources[c].n};
+    }
   }
-  const int tile = opts && opts->tile > 0 ? opts->tile : 8192;
-  // host planner: pair descriptors, work items (tiles of each pair's source)
+  const int item = opts && opts->tile > 0 ? opts->tile : default_item_size();
+  // host planner: pair descriptors; work items (chunks of each pair's source),
+  // emitted in order of (target map, source) so that concurrently running CTAs
+  // share a few target maps in L2; span[p] = the items of pair p.
   std::vector<PairDesc> pd((size_t)n_pairs);
-  std::vector<int32_t> item_off((size_t)n_pairs + 1);
-  std::vector<WorkItem> items;
-  int64_t n_items = 0;
+  std::vector<int64_t> order((size_t)n_pairs);
   for (int64_t p = 0; p < n_pairs; ++p) {
     const int32_t m = pairs[2 * p], c = pairs[2 * p + 1];
     if (m < 0 || m >= n_maps || c < 0 || c >= n_sources)
@@ -462,25 +512,29 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
       return set_error(VGICP_ERR_INVALID_ARG,
                        "pose " + std::to_string(p) + " is not a finite rigid transform");
     pd[(size_t)p] = make_pair_desc(poses + 16 * p, m, c);
-    item_off[(size_t)p] = (int32_t)n_items;
-    n_items += (sources[c].n + tile - 1) / tile;
+    order[(size_t)p] = p;
   }
-  item_off[(size_t)n_pairs] = (int32_t)n_items;
-  if (n_items > INT32_MAX) return set_error(VGICP_ERR_INVALID_ARG, "too many work items");
-  items.resize((size_t)n_items);
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    const int64_t n = sources[pairs[2 * p + 1]].n;
-    int32_t k = item_off[(size_t)p];
-    for (int64_t b = 0; b < n; b += tile, ++k)
-      items[(size_t)k] = WorkItem{(int32_t)p, (int32_t)b, (int32_t)std::min<int64_t>(n, b + tile), 0};
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return pairs[2 * a] != pairs[2 * b] ? pairs[2 * a] < pairs[2 * b]
+                                        : pairs[2 * a + 1] < pairs[2 * b + 1];
+  });
+  std::vector<int2> span((size_t)n_pairs);
+  std::vector<WorkItem> items;
+  for (int64_t q = 0; q < n_pairs; ++q) {
+    const int64_t p = order[(size_t)q];
+    const int64_t n = sd[(size_t)pairs[2 * p + 1]].n;
+    const int32_t first = (int32_t)items.size();
+    for (int64_t b = 0; b < n; b += item)
+      items.push_back(WorkItem{(int32_t)p, (int32_t)b, (int32_t)std::min<int64_t>(n, b + item), 0});
+    span[(size_t)p] = make_int2(first, (int32_t)items.size());
+    if (items.size() > (size_t)INT32_MAX / 2)
+      return set_error(VGICP_ERR_INVALID_ARG, "too many work items");
   }
+  const int64_t n_items = (int64_t)items.size();
   std::vector<MapDesc> md((size_t)n_maps);
   for (int32_t m = 0; m < n_maps; ++m) md[(size_t)m] = make_map_desc(maps[m]);
-  std::vector<SrcDesc> sd((size_t)n_sources);
-  for (int32_t c = 0; c < n_sources; ++c)
-    sd[(size_t)c] = SrcDesc{sources[c].points, sources[c].covs, sources[c].n};
 
-  // one device buffer: descriptors, items, offsets, partials
+  // one device buffer: descriptors, items, spans | status, partials
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -491,8 +545,9 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
   const size_t o_md = take(sizeof(MapDesc) * md.size());
   const size_t o_sd = take(sizeof(SrcDesc) * sd.size());
   const size_t o_items = take(sizeof(WorkItem) * items.size());
-  const size_t o_ioff = take(sizeof(int32_t) * item_off.size());
+  const size_t o_span = take(sizeof(int2) * span.size());
   const size_t upload = off;
+  const size_t o_status = take(sizeof(int32_t));
   const size_t o_part = take(sizeof(double) * kPartialStride * std::max<int64_t>(n_items, 1));
   std::vector<char> host(upload);
   std::memcpy(host.data() + o_pd, pd.data(), sizeof(PairDesc) * pd.size());
@@ -500,33 +555,40 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
   std::memcpy(host.data() + o_sd, sd.data(), sizeof(SrcDesc) * sd.size());
   if (!items.empty())
     std::memcpy(host.data() + o_items, items.data(), sizeof(WorkItem) * items.size());
-  std::memcpy(host.data() + o_ioff, item_off.data(), sizeof(int32_t) * item_off.size());
+  std::memcpy(host.data() + o_span, span.data(), sizeof(int2) * span.size());
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* dev = nullptr;
   VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dev), off, st));
   int rc = VGICP_OK;
-  cudaError_t e = cudaMemcpyAsync(dev, host.data(), upload, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) rc = check_cuda(e, "cudaMemcpyAsync(plan)");
   // (a copy from pageable memory returns once the source has been staged, so
   // `host` may be released when this function returns)
+  cudaError_t e = cudaMemcpyAsync(dev, host.data(), upload, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = check_cuda(e, "cudaMemcpyAsync(plan)");
+  if (rc == VGICP_OK) {
+    e = cudaMemsetAsync(dev + o_status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) rc = check_cuda(e, "cudaMemsetAsync");
+  }
   if (rc == VGICP_OK) {
     LinLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.items = reinterpret_cast<const WorkItem*>(dev + o_items);
     L.n_items = (int32_t)n_items;
+    L.item_size = item;
     L.pairs = reinterpret_cast<const PairDesc*>(dev + o_pd);
     L.maps = reinterpret_cast<const MapDesc*>(dev + o_md);
     L.srcs = reinterpret_cast<const SrcDesc*>(dev + o_sd);
     L.partials = reinterpret_cast<double*>(dev + o_part);
+    L.status = reinterpret_cast<int32_t*>(dev + o_status);
     L.neighbours = neighbours;
+    L.variant = opts ? opts->variant : 0;
     L.grid = opts ? opts->grid : 0;
     L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
     L.ev_stop = opts ? static_cast<cudaEvent_t>(opts->kernel_stop) : nullptr;
     rc = launch_linearize(L, st);
     if (rc == VGICP_OK)
-      rc = launch_reduce(L.partials, reinterpret_cast<const int32_t*>(dev + o_ioff), 0, n_pairs,
-                         out, inliers, st);
+      rc = launch_reduce(L.partials, reinterpret_cast<const int2*>(dev + o_span), 0, n_pairs,
+                         L.status, out, inliers, st);
   }
   e = cudaFreeAsync(dev, st);
   if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");

@@ -195,6 +195,170 @@ __global__ void finalize_kernel(int64_t n_max, const uint32_t* __restrict__ n_vo
   }
 }
 
+// 10 bits per axis of the key, interleaved (a locality order, not a unique code).
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+  x &= 1023u;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+__device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
+  const unsigned long long fm = (1ull << kKeyBits) - 1ull;
+  const uint32_t kx = (uint32_t)((key >> (2 * kKeyBits)) & fm);
+  const uint32_t ky = (uint32_t)((key >> kKeyBits) & fm);
+  const uint32_t kz = (uint32_t)(key & fm);
+  return spread10(kx) | (spread10(ky) << 1) | (spread10(kz) << 2);
+}
+
+// One CTA per (map, chunk): bitonic sort of the chunk's voxels by Morton code in
+// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order.
+constexpr int kSortThreads = 1024;
+__global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
+    const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
+    const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank) {
+  extern __shared__ unsigned long long sk[];
+  const int m = chunks[blockIdx.x].x;
+  const uint32_t V = vbase[m + 1] - vbase[m];
+  const uint32_t lo = (uint32_t)chunks[blockIdx.x].y * kMortonChunk;
+  if (lo >= V) return;
+  const uint32_t cnt = min((uint32_t)kMortonChunk, V - lo);
+  uint32_t N = 1;
+  while (N < cnt) N <<= 1;
+  const uint32_t first = vbase[m] + lo;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+    sk[i] = i < cnt ? (((unsigned long long)morton_of_key(vkeys[first + i]) << 32) | i) : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint32_t q = i ^ j;
+        if (q > i) {
+          const unsigned long long a = sk[i], b = sk[q];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            sk[i] = b;
+            sk[q] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
+    vrank[first + (uint32_t)(sk[i] & 0xFFFFFFFFull)] = first + i;
+}
+
+__global__ void rank_counts_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
+                                   const uint32_t* __restrict__ vrank,
+                                   const uint32_t* __restrict__ vcount,
+                                   uint32_t* __restrict__ gcount) {
+  const int64_t V = *n_vox;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
+       v += (int64_t)gridDim.x * blockDim.x)
+    gcount[vrank[v]] = vcount[v];
+}
+
+// The clouds grouped by voxel, voxels in Morton order, points of a voxel in
+// ascending index: point j of voxel v (at list position pos) goes to
+// goff[vrank[v]] + (pos - voff[v]).
+__global__ void group_kernel(int64_t n_total, const uint32_t* __restrict__ n_valid,
+                             const uint32_t* __restrict__ plist,
+                             const uint32_t* __restrict__ pt_slot, const Slot* __restrict__ slots,
+                             const uint32_t* __restrict__ voff, const uint32_t* __restrict__ vrank,
+                             const uint32_t* __restrict__ goff, const float* __restrict__ pts,
+                             const float* __restrict__ covs, float* __restrict__ gpts,
+                             float* __restrict__ gcovs) {
+  const int64_t n = min(n_total, (int64_t)*n_valid);  // only positions holding a point
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = plist[p];
+    const uint32_t v = slots[pt_slot[j]].vid;
+    const int64_t pos = (int64_t)goff[vrank[v]] + (p - (int64_t)voff[v]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gpts[3 * pos + k] = __ldg(pts + 3 * j + k);
+    const float2* c = reinterpret_cast<const float2*>(covs + 6 * j);
+    float2* g = reinterpret_cast<float2*>(gcovs + 6 * pos);
+    g[0] = __ldg(c);
+    g[1] = __ldg(c + 1);
+    g[2] = __ldg(c + 2);
+  }
+}
+
+__device__ __forceinline__ uint32_t lookup_capacity(uint32_t nvox) {
+  uint32_t c = 16;
+  while (c < 2u * nvox) c <<= 1;
+  return c;
+}
+
+// Per map (blockIdx.y): lookup-table capacity from its voxel count, empty keys.
+__global__ void vslot_init_kernel(const int64_t* __restrict__ slot_base,
+                                  const uint32_t* __restrict__ vbase, VSlot* vslots,
+                                  uint32_t* __restrict__ vmask) {
+  const int m = blockIdx.y;
+  const uint32_t cap = lookup_capacity(vbase[m + 1] - vbase[m]);
+  VSlot* t = vslots + slot_base[m];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+    t[i].key = kEmptyKey;
+  if (blockIdx.x == 0 && threadIdx.x == 0) vmask[m] = cap - 1u;
+}
+
+// Per voxel: insert key and Gaussian into its map's lookup table.
+__global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
+                                    int32_t n_maps, const uint32_t* __restrict__ vbase,
+                                    const int64_t* __restrict__ slot_base,
+                                    const uint32_t* __restrict__ vmask,
+                                    const unsigned long long* __restrict__ vkeys,
+                                    const float4* __restrict__ recs, int32_t max_probe,
+                                    VSlot* vslots, int32_t* status) {
+  const int64_t V = *n_vox;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_maps;  // last m with vbase[m] <= v
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (vbase[mid] <= (uint32_t)v) lo = mid; else hi = mid;
+    }
+    const unsigned long long key = vkeys[v];
+    const unsigned long long fm = (1ull << kKeyBits) - 1ull;
+    const int kx = (int)((key >> (2 * kKeyBits)) & fm) - kKeyBias;
+    const int ky = (int)((key >> kKeyBits) & fm) - kKeyBias;
+    const int kz = (int)(key & fm) - kKeyBias;
+    const uint32_t mask = vmask[lo];
+    VSlot* t = vslots + slot_base[lo];
+    uint32_t h = hash_key(kx, ky, kz) & mask;
+    bool placed = false;
+    for (int p = 0; p < max_probe; ++p) {
+      if (atomicCAS(&t[h].key, kEmptyKey, key) == kEmptyKey) {
+        placed = true;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    if (!placed) {
+      set_status(status, VGICP_ERR_HASH_FULL);
+      continue;
+    }
+    const float4 r0 = recs[3 * v], r1 = recs[3 * v + 1], r2 = recs[3 * v + 2];
+    VSlot& sl = t[h];
+    sl.vid = (uint32_t)v;
+    sl.count = __float_as_uint(r0.w);
+    sl.mu[0] = r0.x;
+    sl.mu[1] = r0.y;
+    sl.mu[2] = r0.z;
+    sl.pad0 = 0.0f;
+    sl.cov[0] = r1.x;
+    sl.cov[1] = r1.y;
+    sl.cov[2] = r1.z;
+    sl.cov[3] = r1.w;
+    sl.cov[4] = r2.x;
+    sl.cov[5] = r2.y;
+    sl.pad1[0] = 0.0f;
+    sl.pad1[1] = 0.0f;
+  }
+}
+
 // ---- exclusive scan of uint32 (three phases) --------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 8;
@@ -318,7 +482,10 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   if (n == 0) {
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_num_voxels, 0, sizeof(uint32_t), st));
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vbase, 0, sizeof(uint32_t) * (s->n_maps + 1), st));
+    vslot_init_kernel<<<dim3(1, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
+                                                              s->d_vslots, s->d_vmask);
     VGICP_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
     return VGICP_OK;
   }
   const float inv_r = (float)(1.0 / s->resolution);
@@ -337,15 +504,47 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
                                                             s->d_flag, s->d_num_voxels,
                                                             s->d_vbase);
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
-  rc = launch_exclusive_scan(s->d_vcount, s->d_voff, n, s->d_num_voxels, s->d_scan_tmp, nullptr,
-                             st);
+  rc = launch_exclusive_scan(s->d_vcount, s->d_voff, n, s->d_num_voxels, s->d_scan_tmp,
+                             s->d_num_valid, st);
   if (rc != VGICP_OK) return rc;
   scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_voff, s->d_vfill,
                                          s->d_plist);
   finalize_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
                                           s->d_voff, s->d_plist, s->d_recs);
+  int64_t max_cap = 16;
+  for (int32_t m = 0; m < s->n_maps; ++m)
+    max_cap = std::max<int64_t>(max_cap, (m + 1 < s->n_maps ? s->vslot_base[m + 1] : s->vcap_total) -
+                                             s->vslot_base[m]);
+  const unsigned gx = (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
+  vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
+                                                             s->d_vslots, s->d_vmask);
+  vslot_insert_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, s->n_maps, s->d_vbase,
+                                              s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
+                                              s->max_probe, s->d_vslots, s->d_status);
+  // voxel-grouped, spatially ordered copy of the clouds (the sources of map-sourced
+  // factors): d_flag and d_vfill are free scratch at this point
+  uint32_t* vrank = s->d_flag;
+  uint32_t* gcount = s->d_vfill;
+  static bool sort_attr = false;
+  if (!sort_attr) {
+    VGICP_CUDA_TRY(cudaFuncSetAttribute(morton_sort_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(unsigned long long) * kMortonChunk)));
+    sort_attr = true;
+  }
+  morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kMortonChunk, st>>>(
+      s->d_chunks, s->d_vbase, s->d_vkeys, vrank);
+  rank_counts_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_vcount, gcount);
   VGICP_CUDA_TRY(cudaGetLastError());
-  count_launches(7);  // insert, first, assign, vbase, scatter, finalize (+ init above: 1)
+  rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp, nullptr, st);
+  if (rc != VGICP_OK) return rc;
+  group_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_valid, s->d_plist, s->d_pt_slot, s->d_slots,
+                                       s->d_voff, vrank, s->d_goff, points, covs, s->d_gpts,
+                                       s->d_gcovs);
+  VGICP_CUDA_TRY(cudaGetLastError());
+  // insert, first, assign, vbase, scatter, finalize, vslot init/insert, sort, rank counts,
+  // group (+ init: 1)
+  count_launches(11);
   return VGICP_OK;
 }
 

@@ -29,19 +29,36 @@ constexpr int kKeyMin = -kKeyBias;             // valid k: [-2^20, 2^20)
 constexpr int kKeyMax = kKeyBias - 1;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
-// Voxel record: 3 x float4 = 48 B.
+// Voxel record: 3 x float4 = 48 B (kept for export and tests).
 //   r0 = (mu'.x, mu'.y, mu'.z, bits(N)), r1 = (C'xx, C'xy, C'xz, C'yy),
 //   r2 = (C'yz, C'zz, 0, 0)
 constexpr int kRecordF4 = 3;
 
+// Lookup table slot with the voxel Gaussian inline (64 B, 64-B aligned): one
+// probe is two independent 256-bit loads, so a lookup costs one round trip.
+//   bytes  0..31: key (u64), vid (u32), count (u32), mu' (3 x f32), pad
+//   bytes 32..63: C' (6 x f32, xx xy xz yy yz zz), pad
+// Each map's table has capacity next_pow2(max(16, 2 V)) (decided on the device
+// after the voxels are counted) inside a region sized for the worst case V = n.
+struct __align__(64) VSlot {
+  unsigned long long key;
+  uint32_t vid;
+  uint32_t count;
+  float mu[3];
+  float pad0;
+  float cov[6];
+  float pad1[2];
+};
+static_assert(sizeof(VSlot) == 64, "VSlot is 64 B");
+
 // Per-map descriptor read by the linearize kernels.
 struct MapDesc {
-  const Slot* slots;   // this map's table (cap slots)
-  const float4* recs;  // global record array (vids are global)
-  uint32_t mask;       // cap - 1
+  const VSlot* vslots;    // this map's lookup table
+  const uint32_t* vmask;  // device: its capacity - 1
   int32_t max_probe;
-  float inv_r;         // float32(1 / r)
-  float margin_scale;  // inv_r * 2^-21 (see source_key)
+  float inv_r;            // float32(1 / r)
+  float margin_scale;     // inv_r * 2^-21 (see source_key)
+  int32_t pad;
   double r;
   const uint32_t* vbase;  // first global voxel index of this map (device)
 };
@@ -63,6 +80,10 @@ struct SrcDesc {
   const float* covs;  // n x 6
   int64_t n;
 };
+
+// Voxels of a map are put in Morton order in chunks of this many (one CTA sorts
+// one chunk in shared memory).
+constexpr int kMortonChunk = 16384;
 
 // Work item: points [begin, end) of pair `pair`.
 struct __align__(16) WorkItem {

@@ -35,13 +35,18 @@ struct MapSet {
   std::vector<int64_t> point_off;  // n_maps + 1
   std::vector<int64_t> slot_base;  // n_maps
   std::vector<uint32_t> cap;       // n_maps
+  std::vector<int64_t> vslot_base; // n_maps: lookup-table region (worst case V = n)
+  int64_t vcap_total = 0;
   // device: per-map metadata
   int64_t* d_point_off = nullptr;  // n_maps + 1
   int64_t* d_slot_base = nullptr;  // n_maps
+  int64_t* d_vslot_base = nullptr; // n_maps
   uint32_t* d_cap_mask = nullptr;  // n_maps
   uint32_t* d_vbase = nullptr;     // n_maps + 1: first global voxel index of each map
   // device: the maps
-  Slot* d_slots = nullptr;                  // cap_total
+  Slot* d_slots = nullptr;                  // cap_total (build table)
+  VSlot* d_vslots = nullptr;                // vcap_total (lookup table, inline records)
+  uint32_t* d_vmask = nullptr;              // n_maps: lookup-table capacity - 1
   float4* d_recs = nullptr;                 // n_total * 3 (V <= n_total)
   unsigned long long* d_vkeys = nullptr;    // n_total (packed keys by voxel)
   int32_t* d_status = nullptr;              // 1
@@ -52,8 +57,14 @@ struct MapSet {
   uint32_t* d_voff = nullptr;     // n_total
   uint32_t* d_vfill = nullptr;    // n_total
   uint32_t* d_plist = nullptr;    // n_total
+  float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
+  float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
+  uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
+  int2* d_chunks = nullptr;       // (map, chunk) pairs for the Morton sort
+  int32_t n_chunks = 0;
   uint32_t* d_scan_tmp = nullptr; // scan block sums
   uint32_t* d_num_voxels = nullptr;  // 1 (total V)
+  uint32_t* d_num_valid = nullptr;   // 1 (points placed in a voxel)
   size_t scan_tmp_elems = 0;
   void* d_block = nullptr;        // single allocation holding everything above
 };
@@ -79,9 +90,9 @@ size_t scan_tmp_elems(int64_t n_max);
 
 // ---- kernels (vgicp_linearize.cu) ----------------------------------------
 struct LinLaunch {
-  const WorkItem* items;     // null: uniform tiles of pair 0 (single factor)
+  const WorkItem* items;     // null: uniform items of pair 0 (single factor)
   int32_t n_items;
-  int32_t tile;              // uniform-tile mode
+  int32_t item_size;         // uniform-item mode: points per item
   const PairDesc* pairs;     // null: use `single`
   const MapDesc* maps;       // null: use `single_map`
   const SrcDesc* srcs;       // null: use `single_src`
@@ -89,19 +100,28 @@ struct LinLaunch {
   MapDesc single_map;
   SrcDesc single_src;
   double* partials;          // n_items x kPartialStride
+  int32_t* status;           // device int: nonzero after an internal wait timeout
   int32_t* corr_out;
   int32_t* qkey_out;
   int32_t neighbours;
-  int32_t grid;
-  int32_t block;
+  int32_t variant;           // 1-neighbour kernel: 1 per-point, 2 staged (0 = default)
+  int32_t grid;              // 0 = automatic
   cudaEvent_t ev_start;      // optional, recorded around the kernel
   cudaEvent_t ev_stop;
 };
 int launch_linearize(const LinLaunch& L, cudaStream_t st);
 
-// Sum the partials of each pair's items [item_off[p], item_off[p+1]) in order.
-int launch_reduce(const double* partials, const int32_t* item_off, int32_t n_items_single,
-                  int64_t n_pairs, double* out, int64_t* inliers, cudaStream_t st);
+// Points per work item and the persistent grid the linearize kernel uses.
+int default_item_size();
+int linearize_grid(int neighbours, int variant);
+int default_variant();
+
+// Sum each pair's partials over its items [span[p].x, span[p].y) in order and
+// expand to the 43-double result; span == nullptr means one pair over all
+// n_items_single items.  A nonzero *status turns every output into NaN.
+int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
+                  int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
+                  cudaStream_t st);
 
 int device_sm_count();
 

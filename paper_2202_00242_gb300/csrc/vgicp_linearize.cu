@@ -16,9 +16,18 @@
 //   b   += [ u x mu ; -u ]
 //   H   += [[ [mu]x^T W' [mu]x , [mu]x W' ], [ ., W' ]]
 // The 28 unique terms and the inlier count are accumulated per thread in
-// float32, reduced across the warp in float32, across warps in binary64, and
-// written as one binary64 partial per work item; a second kernel sums each
-// pair's partials in item order.  The result is deterministic.
+// float32 over a work item (up to 16K points of one pair), reduced across the
+// warp in float32, across warps in binary64, and written as one binary64
+// partial per work item; a second kernel sums each pair's partials in item
+// order.  The result is deterministic.
+//
+// 1-neighbour kernel (the paper's lookup): a producer warp streams tiles of
+// source points and covariances into shared memory with bulk asynchronous
+// copies (cp.async.bulk + mbarrier, 4 stages); each consumer warp looks up the
+// voxels of its 64 points, compacts the hits into a per-warp list with the
+// voxel records staged in shared memory, then evaluates the terms from shared
+// memory only, so lanes idle on misses do not cost arithmetic.
+// 27-neighbour kernel: one point per thread, the 27 lookups in a loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,13 +39,25 @@
 namespace vgicp {
 namespace {
 
-constexpr int kLinThreads = 256;
+constexpr int kSimpleThreads = 256;
 
 struct Pose32 {
   float R[9];
   float t[3];
   float tmax;
 };
+
+// floor(q_a / r) with q = R64 mu + t64 in binary64 (the rare near-face path).
+__device__ __noinline__ int axis_key_f64(const PairDesc* pd, const MapDesc& md, int a, float x,
+                                         float y, float z) {
+  double s = __dmul_rn(pd->R64[3 * a + 0], (double)x);
+  s = __dadd_rn(s, __dmul_rn(pd->R64[3 * a + 1], (double)y));
+  s = __dadd_rn(s, __dmul_rn(pd->R64[3 * a + 2], (double)z));
+  s = __dadd_rn(s, pd->t64[a]);
+  double k = floor(__ddiv_rn(s, md.r));
+  k = fmin(fmax(k, -2147483648.0), 2147483647.0);
+  return (int)k;
+}
 
 // Key of the transformed source point, exact w.r.t. the binary64 definition
 // floor((R64 mu + t64) / r).  Float32 bound: |q32 - q64| <= 2^-22 S with
@@ -59,33 +80,65 @@ __device__ __forceinline__ void source_key(const Pose32& P, const PairDesc* pd, 
   kz = clamp_to_int(fz);
   if (ax | ay | az) {
     // binary64, evaluated as ((R0 x + R1 y) + R2 z) + t without contraction
-    const double dxp = x, dyp = y, dzp = z;
-    int* kk[3] = {&kx, &ky, &kz};
-    const bool amb[3] = {ax, ay, az};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (!amb[a]) continue;
-      double s = __dmul_rn(pd->R64[3 * a + 0], dxp);
-      s = __dadd_rn(s, __dmul_rn(pd->R64[3 * a + 1], dyp));
-      s = __dadd_rn(s, __dmul_rn(pd->R64[3 * a + 2], dzp));
-      s = __dadd_rn(s, pd->t64[a]);
-      double k = floor(__ddiv_rn(s, md.r));
-      k = fmin(fmax(k, -2147483648.0), 2147483647.0);
-      *kk[a] = (int)k;
-    }
+    if (ax) kx = axis_key_f64(pd, md, 0, x, y, z);
+    if (ay) ky = axis_key_f64(pd, md, 1, x, y, z);
+    if (az) kz = axis_key_f64(pd, md, 2, x, y, z);
   }
 }
 
-__device__ __forceinline__ int lookup(const MapDesc& md, int kx, int ky, int kz) {
+// Two independent 256-bit loads: one probe of a 64-B lookup slot.
+#ifndef VGICP_LD_FLAVOR
+#define VGICP_LD_FLAVOR 0
+#endif
+__device__ __forceinline__ void ld_v8(const void* p, uint64_t policy, uint32_t (&w)[8]) {
+#if VGICP_LD_FLAVOR == 0
+  asm("ld.global.nc.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+        "=r"(w[7])
+      : "l"(p), "l"(policy));
+#elif VGICP_LD_FLAVOR == 1
+  asm("ld.global.cg.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+        "=r"(w[7])
+      : "l"(p), "l"(policy));
+#else
+  asm("ld.global.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+        "=r"(w[7])
+      : "l"(p), "l"(policy));
+#endif
+}
+__device__ __forceinline__ unsigned long long slot_key(const uint32_t (&a)[8]) {
+  return (unsigned long long)a[0] | ((unsigned long long)a[1] << 32);
+}
+__device__ __forceinline__ uint64_t policy_evict_last_l() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Lookup of key (kx, ky, kz) in a map's inline table; on a hit returns the
+// global voxel id and the voxel Gaussian as r0 = (mu', -), r1, r2 (record layout).
+__device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, int ky, int kz,
+                                      uint64_t pol, float4& r0, float4& r1, float4& r2) {
   if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) return -1;
   const unsigned long long key = pack_key(kx, ky, kz);
-  const ulonglong2* slots = reinterpret_cast<const ulonglong2*>(md.slots);
-  uint32_t h = hash_key(kx, ky, kz) & md.mask;
+  uint32_t h = hash_key(kx, ky, kz) & mask;
   for (int p = 0; p < md.max_probe; ++p) {
-    const ulonglong2 s = __ldg(slots + h);
-    if (s.x == key) return (int)(uint32_t)s.y;
-    if (s.x == kEmptyKey) return -1;
-    h = (h + 1) & md.mask;
+    uint32_t a[8], b[8];
+    const VSlot* t = md.vslots + h;
+    ld_v8(t, pol, a);
+    ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
+    const unsigned long long k = slot_key(a);
+    if (k == key) {
+      r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
+      r1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
+                       __uint_as_float(b[3]));
+      r2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
+      return (int)a[2];
+    }
+    if (k == kEmptyKey) return -1;
+    h = (h + 1) & mask;
   }
   return -1;
 }
@@ -166,24 +219,423 @@ __device__ __forceinline__ void add_term(float* acc, const Pose32& P, float x, f
   acc[28] += 1.0f;
 }
 
+
+// Launch-shape constants (compile-time; overridable for tuning builds).
+#ifndef VGICP_NCW
+#define VGICP_NCW 4
+#endif
+#ifndef VGICP_PTS_PER_LANE
+#define VGICP_PTS_PER_LANE 2
+#endif
+#ifndef VGICP_STAGES
+#define VGICP_STAGES 4
+#endif
+#ifndef VGICP_MIN_BLOCKS
+#define VGICP_MIN_BLOCKS 3
+#endif
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and bulk asynchronous copy (global -> shared)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes
+// (or the hint expires) instead of spinning on the issue slots.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up after 2 s (a bug, never a normal state).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+// L2 policies: the source stream is read once per factor (evict first), while
+// the lookup tables are re-read by every source point of the factors that
+// target them (evict last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+// 4-byte asynchronous copy global -> shared, completion tracked by an mbarrier
+// through cp_async_arrive_noinc.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void consumer_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(VGICP_NCW * 32) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// 1-neighbour kernel with shared-memory staging
+// ---------------------------------------------------------------------------
+namespace tma {
+constexpr int kNCW = VGICP_NCW;               // consumer warps
+constexpr int kThreads = (kNCW + 1) * 32;     // + one producer warp
+constexpr int kPtsPerLane = VGICP_PTS_PER_LANE;
+constexpr int kWarpPts = 32 * kPtsPerLane;    // 64 points per consumer warp
+constexpr int kTile = kNCW * kWarpPts;        // 256 points per tile
+constexpr int kStages = VGICP_STAGES;
+constexpr int kXyzBytes = kTile * 12 + 32;    // + room for a 16-B alignment shift
+constexpr int kCovBytes = kTile * 24 + 32;
+constexpr int kFirst = 1, kLast = 2;
+
+struct TileDesc {
+  int32_t pair, begin, n, item, flags, xyz_off, cov_off, pad;
+};
+
+struct __align__(16) Smem {
+  float4 hits[kNCW][kWarpPts * 3];            // staged voxel records of hits
+  unsigned char xyz[kStages][kXyzBytes];
+  unsigned char cov[kStages][kCovBytes];
+  TileDesc desc[kStages];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  float red[kNCW][32];
+};
+static_assert(kXyzBytes % 16 == 0 && kCovBytes % 16 == 0, "bulk-copy alignment");
+
+// Copy the float range [gs, ge) of global memory into shared memory at
+// dst + (gs - floor16(gs)): the 16-B aligned interior with one bulk copy
+// (issue_bulk), the ragged head and tail (< 16 B each) with 4-byte cp.async
+// (!issue_bulk).  Returns the bulk bytes.
+__device__ __forceinline__ uint32_t stage_range(unsigned char* dst, uintptr_t gs, uintptr_t ge,
+                                                uint64_t* bar, bool issue_bulk, uint64_t policy) {
+  const uintptr_t g0 = gs & ~(uintptr_t)15;
+  const uintptr_t a = (gs + 15) & ~(uintptr_t)15;
+  const uintptr_t b = ge & ~(uintptr_t)15;
+  uint32_t bulk = 0;
+  uintptr_t h1 = ge, t0 = ge;
+  if (b > a) {
+    bulk = (uint32_t)(b - a);
+    h1 = a;
+    t0 = b;
+    if (issue_bulk) bulk_g2s(dst + (a - g0), reinterpret_cast<const void*>(a), bulk, bar, policy);
+  }
+  if (!issue_bulk) {
+    for (uintptr_t p = gs; p < h1; p += 4)
+      cp_async4(dst + (p - g0), reinterpret_cast<const void*>(p));
+    for (uintptr_t p = t0; p < ge; p += 4)
+      cp_async4(dst + (p - g0), reinterpret_cast<const void*>(p));
+  }
+  return bulk;
+}
+
+__device__ __forceinline__ void item_bounds(const LinLaunch& L, int it, int& pair, int& b,
+                                            int& e) {
+  if (L.items) {
+    const WorkItem w = L.items[it];
+    pair = w.pair;
+    b = w.begin;
+    e = w.end;
+  } else {
+    pair = 0;
+    b = it * L.item_size;
+    e = (int)min((int64_t)b + L.item_size, L.single_src.n);
+  }
+}
+
+// Warp reduce-scatter of 32 values: afterwards lane l holds the warp total of v[l]
+// (31 shuffles instead of 5 per value).
+template <int W>
+__device__ __forceinline__ void rs_step(float* v, int lane) {
+  const bool up = (lane & W) != 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const float send = up ? v[j] : v[j + W];
+    const float keep = up ? v[j + W] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, W);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kernel(const __grid_constant__ LinLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&S.full[s], 2);  // producer arrive + cp.async completion arrive
+      mbar_init(&S.empty[s], kNCW);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == kNCW) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    const uint64_t stream_pol = policy_evict_first();
+    uint32_t u = 0;  // tiles issued
+    bool ok = true;
+    for (int it = blockIdx.x; it < L.n_items && ok; it += gridDim.x) {
+      int pair, b, e;
+      item_bounds(L, it, pair, b, e);
+      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
+      for (int t0 = b; t0 < e; t0 += kTile) {
+        const int s = u % kStages;
+        if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        const int n = min(kTile, e - t0);
+        const uintptr_t xs = reinterpret_cast<uintptr_t>(sd.pts + 3 * (int64_t)t0);
+        const uintptr_t cs = reinterpret_cast<uintptr_t>(sd.covs + 6 * (int64_t)t0);
+        // head/tail cp.async and the descriptor, then the two arrivals, then bulk
+        const uintptr_t xe = xs + 12 * (uintptr_t)n, ce = cs + 24 * (uintptr_t)n;
+        const uint32_t tx = stage_range(S.xyz[s], xs, xe, &S.full[s], false, stream_pol) +
+                            stage_range(S.cov[s], cs, ce, &S.full[s], false, stream_pol);
+        TileDesc d;
+        d.pair = pair;
+        d.begin = t0;
+        d.n = n;
+        d.item = it;
+        d.flags = (t0 == b ? kFirst : 0) | (t0 + kTile >= e ? kLast : 0);
+        d.xyz_off = (int)(xs & 15);
+        d.cov_off = (int)(cs & 15);
+        d.pad = 0;
+        S.desc[s] = d;
+        cp_async_arrive_noinc(&S.full[s]);
+        mbar_arrive_expect_tx(&S.full[s], tx);
+        stage_range(S.xyz[s], xs, xe, &S.full[s], true, stream_pol);
+        stage_range(S.cov[s], cs, ce, &S.full[s], true, stream_pol);
+        ++u;
+      }
+    }
+    if (ok) {
+      const int s = u % kStages;
+      if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1)) ok = false;
+      if (ok) {
+        S.desc[s].n = -1;
+        mbar_arrive(&S.full[s]);
+        mbar_arrive(&S.full[s]);
+        ++u;
+      }
+    }
+    if (!ok) {
+      atomicExch(L.status, 1);
+      // let copies already in flight land before the block exits
+      for (uint32_t v = (u > kStages ? u - kStages : 0); v < u; ++v)
+        mbar_wait(&S.full[v % kStages], (v / kStages) & 1);
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  float acc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+  Pose32 P;
+  MapDesc md;
+  const PairDesc* pd = nullptr;
+  uint32_t vbase = 0, mask = 0;
+  float4* H = S.hits[warp];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t map_pol = policy_evict_last();
+
+  for (uint32_t u = 0;; ++u) {
+    const int s = u % kStages;
+    if (!mbar_wait(&S.full[s], (u / kStages) & 1)) {
+      atomicExch(L.status, 1);
+      break;
+    }
+    const TileDesc d = S.desc[s];
+    if (d.n < 0) break;
+    if (d.flags & kFirst) {
+      pd = L.pairs ? L.pairs + d.pair : &L.single;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
+      P.t[0] = pd->t[0];
+      P.t[1] = pd->t[1];
+      P.t[2] = pd->t[2];
+      P.tmax = pd->tmax;
+      md = L.maps ? L.maps[pd->map] : L.single_map;
+      mask = *md.vmask;
+      if (L.corr_out) vbase = *md.vbase;
+    }
+    const float* X = reinterpret_cast<const float*>(S.xyz[s] + d.xyz_off);
+    const float* C = reinterpret_cast<const float*>(S.cov[s] + d.cov_off);
+
+    // ---- lookup: key, first probe (two 256-bit loads) of every point, resolve ----
+    int idx[kPtsPerLane];
+    int kx[kPtsPerLane], ky[kPtsPerLane], kz[kPtsPerLane];
+    bool live[kPtsPerLane];
+    unsigned long long key[kPtsPerLane];
+    uint32_t h[kPtsPerLane];
+    uint32_t sa[kPtsPerLane][8], sb[kPtsPerLane][8];
+#pragma unroll
+    for (int k = 0; k < kPtsPerLane; ++k) {
+      idx[k] = warp * kWarpPts + k * 32 + lane;
+      live[k] = idx[k] < d.n;
+      kx[k] = ky[k] = kz[k] = kKeyMin - 1;
+      if (live[k]) {
+        const float x = X[3 * idx[k]], y = X[3 * idx[k] + 1], z = X[3 * idx[k] + 2];
+        const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+        const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+        const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+        source_key(P, pd, md, x, y, z, qx, qy, qz, kx[k], ky[k], kz[k]);
+        live[k] = key_in_range(kx[k]) && key_in_range(ky[k]) && key_in_range(kz[k]);
+      }
+      key[k] = live[k] ? pack_key(kx[k], ky[k], kz[k]) : kEmptyKey;
+      h[k] = hash_key(kx[k], ky[k], kz[k]) & mask;
+      if (live[k]) {
+        ld_v8(md.vslots + h[k], map_pol, sa[k]);
+        ld_v8(reinterpret_cast<const char*>(md.vslots + h[k]) + 32, map_pol, sb[k]);
+      } else {
+        sa[k][0] = sa[k][1] = 0xFFFFFFFFu;
+      }
+    }
+    int vid[kPtsPerLane];
+    float4 r0[kPtsPerLane], r1[kPtsPerLane], r2[kPtsPerLane];
+#pragma unroll
+    for (int k = 0; k < kPtsPerLane; ++k) {
+      vid[k] = -1;
+      if (live[k]) {
+        unsigned long long t = slot_key(sa[k]);
+        uint32_t hh = h[k];
+        for (int p = 1; t != key[k] && t != kEmptyKey && p < md.max_probe; ++p) {
+          hh = (hh + 1) & mask;
+          ld_v8(md.vslots + hh, map_pol, sa[k]);
+          ld_v8(reinterpret_cast<const char*>(md.vslots + hh) + 32, map_pol, sb[k]);
+          t = slot_key(sa[k]);
+        }
+        if (t == key[k]) {
+          vid[k] = (int)sa[k][2];
+          r0[k] = make_float4(__uint_as_float(sa[k][4]), __uint_as_float(sa[k][5]),
+                              __uint_as_float(sa[k][6]), 0.f);
+          r1[k] = make_float4(__uint_as_float(sb[k][0]), __uint_as_float(sb[k][1]),
+                              __uint_as_float(sb[k][2]), __uint_as_float(sb[k][3]));
+          r2[k] = make_float4(__uint_as_float(sb[k][4]), __uint_as_float(sb[k][5]), 0.f, 0.f);
+        }
+      }
+      if (idx[k] < d.n && (L.corr_out || L.qkey_out)) {
+        const int64_t p = (int64_t)d.begin + idx[k];
+        if (L.corr_out) L.corr_out[p] = vid[k] < 0 ? -1 : (int)((uint32_t)vid[k] - vbase);
+        if (L.qkey_out) {
+          L.qkey_out[3 * p + 0] = kx[k];
+          L.qkey_out[3 * p + 1] = ky[k];
+          L.qkey_out[3 * p + 2] = kz[k];
+        }
+      }
+    }
+    // ---- stage the records of the hits, compacted per warp ----
+    int nh = 0;
+#pragma unroll
+    for (int k = 0; k < kPtsPerLane; ++k) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, vid[k] >= 0);
+      if (vid[k] >= 0) {
+        const int pos = nh + __popc(m & lt_mask);
+        H[3 * pos + 0] = make_float4(r0[k].x, r0[k].y, r0[k].z, __int_as_float(idx[k]));
+        H[3 * pos + 1] = r1[k];
+        H[3 * pos + 2] = r2[k];
+      }
+      nh += __popc(m);
+    }
+    __syncwarp();
+    // ---- terms of the hits, from shared memory ----
+    for (int j = lane; j < nh; j += 32) {
+      const float4 e0 = H[3 * j], e1 = H[3 * j + 1], e2 = H[3 * j + 2];
+      const int i = __float_as_int(e0.w);
+      const float x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+      const float2* cv = reinterpret_cast<const float2*>(C + 6 * i);
+      const float2 c01 = cv[0], c23 = cv[1], c45 = cv[2];
+      const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
+      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+      add_term(acc, P, x, y, z, c, qx, qy, qz, e0, e1, e2);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.empty[s]);
+
+    if (d.flags & kLast) {
+      rs_step<16>(acc, lane);
+      rs_step<8>(acc, lane);
+      rs_step<4>(acc, lane);
+      rs_step<2>(acc, lane);
+      rs_step<1>(acc, lane);
+      S.red[warp][lane] = acc[0];
+      consumer_bar();
+      if (warp == 0 && lane < kAcc) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kNCW; ++w) t += (double)S.red[w][lane];
+        L.partials[(int64_t)d.item * kPartialStride + lane] = t;
+      }
+      consumer_bar();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+    }
+  }
+}
+
+}  // namespace tma
+
+// ---------------------------------------------------------------------------
+// One point per thread (1 or 27 neighbours); the lookups and records come from
+// global memory through L1.
+// ---------------------------------------------------------------------------
 template <int NEIGH>
-__global__ void __launch_bounds__(kLinThreads, 2)
-    linearize_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ float red[kLinThreads / 32][kAcc];
+__global__ void __launch_bounds__(kSimpleThreads, 2)
+    linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
+  __shared__ float red[kSimpleThreads / 32][kAcc];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   for (int it = blockIdx.x; it < L.n_items; it += gridDim.x) {
     int pair, begin, end;
-    if (L.items) {
-      const WorkItem w = L.items[it];
-      pair = w.pair;
-      begin = w.begin;
-      end = w.end;
-    } else {
-      pair = 0;
-      begin = it * L.tile;
-      end = (int)min((int64_t)begin + L.tile, L.single_src.n);
-    }
+    tma::item_bounds(L, it, pair, begin, end);
     const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
     Pose32 P;
 #pragma unroll
@@ -194,6 +646,8 @@ __global__ void __launch_bounds__(kLinThreads, 2)
     P.tmax = pd->tmax;
     const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
     const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
+    const uint32_t mask = *md.vmask;
+    const uint64_t pol = policy_evict_last_l();
     uint32_t vbase = 0;
     if (L.corr_out) vbase = *md.vbase;
 
@@ -212,40 +666,33 @@ __global__ void __launch_bounds__(kLinThreads, 2)
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
       int kx, ky, kz;
       source_key(P, pd, md, x, y, z, qx, qy, qz, kx, ky, kz);
-      if (NEIGH == 1) {
-        const int vid = lookup(md, kx, ky, kz);
-        if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-        if (L.qkey_out) {
-          L.qkey_out[3 * (int64_t)p + 0] = kx;
-          L.qkey_out[3 * (int64_t)p + 1] = ky;
-          L.qkey_out[3 * (int64_t)p + 2] = kz;
-        }
-        if (vid < 0) continue;
-        const float4* rec = md.recs + 3 * (int64_t)vid;
-        add_term(acc, P, x, y, z, c, qx, qy, qz, __ldg(rec), __ldg(rec + 1), __ldg(rec + 2));
-      } else {
-        if (L.corr_out) {
-          const int own = lookup(md, kx, ky, kz);
-          L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
-        }
-        if (L.qkey_out) {
-          L.qkey_out[3 * (int64_t)p + 0] = kx;
-          L.qkey_out[3 * (int64_t)p + 1] = ky;
-          L.qkey_out[3 * (int64_t)p + 2] = kz;
-        }
-        for (int dz = -1; dz <= 1; ++dz)
-          for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int vid = lookup(md, kx + dx, ky + dy, kz + dz);
-              if (vid < 0) continue;
-              const float4* rec = md.recs + 3 * (int64_t)vid;
-              add_term(acc, P, x, y, z, c, qx, qy, qz, __ldg(rec), __ldg(rec + 1),
-                       __ldg(rec + 2));
-            }
+      if (L.qkey_out) {
+        L.qkey_out[3 * (int64_t)p + 0] = kx;
+        L.qkey_out[3 * (int64_t)p + 1] = ky;
+        L.qkey_out[3 * (int64_t)p + 2] = kz;
       }
+      if (NEIGH == 1) {
+        float4 a0, a1, a2;
+        const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+        if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+        if (vid >= 0) add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+        continue;
+      }
+      if (L.corr_out) {
+        float4 a0, a1, a2;
+        const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+        L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
+      }
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            float4 a0, a1, a2;
+            const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
+            if (vid < 0) continue;
+            add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+          }
     }
 
-    // warp: float32 butterfly; block: binary64 across warps
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
       float v = acc[k];
@@ -268,20 +715,20 @@ __global__ void __launch_bounds__(kLinThreads, 2)
 }
 
 // One warp per pair: lane k sums term k over the pair's items in order.
-__global__ void reduce_kernel(const double* __restrict__ partials,
-                              const int32_t* __restrict__ item_off, int32_t n_items_single,
-                              int64_t n_pairs, double* __restrict__ out,
+__global__ void reduce_kernel(const double* __restrict__ partials, const int2* __restrict__ span,
+                              int32_t n_items_single, int64_t n_pairs,
+                              const int32_t* __restrict__ status, double* __restrict__ out,
                               int64_t* __restrict__ inliers) {
   const int64_t pair = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
-  const int32_t a = item_off ? item_off[pair] : 0;
-  const int32_t b = item_off ? item_off[pair + 1] : n_items_single;
+  const int32_t a = span ? span[pair].x : 0;
+  const int32_t b = span ? span[pair].y : n_items_single;
   double s = 0.0;
   if (lane < kAcc)
     for (int32_t it = a; it < b; ++it) s += partials[(int64_t)it * kPartialStride + lane];
+  if (status && *status != 0) s = __longlong_as_double(0x7FF8000000000000ll);  // NaN
   double* o = out + pair * 43;
-  // H_ww (sym), H_wv / H_vw, H_vv (sym), b, err
   constexpr int ww_r[6] = {0, 0, 0, 1, 1, 2}, ww_c[6] = {0, 1, 2, 1, 2, 2};
   if (lane < 6) {
     o[6 * ww_r[lane] + ww_c[lane]] = s;
@@ -299,36 +746,57 @@ __global__ void reduce_kernel(const double* __restrict__ partials,
   } else if (lane == 27) {
     o[42] = s;
   } else if (lane == 28) {
-    inliers[pair] = (int64_t)llrint(s);
+    inliers[pair] = (status && *status != 0) ? -1 : (int64_t)llrint(s);
   }
 }
 
 }  // namespace
 
+int default_item_size() { return 16384; }
+
+int default_variant() { return 1; }
+
+int linearize_grid(int neighbours, int variant) {
+  if (variant == 0) variant = default_variant();
+  return device_sm_count() * ((neighbours == 27 || variant == 1) ? 2 : VGICP_MIN_BLOCKS);
+}
+
 int launch_linearize(const LinLaunch& L, cudaStream_t st) {
   if (L.n_items <= 0) return VGICP_OK;
-  const int block = L.block > 0 ? L.block : kLinThreads;
-  if (block != kLinThreads) return set_error(VGICP_ERR_INVALID_ARG, "unsupported block size");
-  int grid = L.grid > 0 ? L.grid : device_sm_count() * 2;
+  const int variant = L.variant ? L.variant : default_variant();
+  int grid = L.grid > 0 ? L.grid : linearize_grid(L.neighbours, variant);
   grid = std::min(grid, L.n_items);
   if (L.ev_start) VGICP_CUDA_TRY(cudaEventRecord(L.ev_start, st));
-  if (L.neighbours == 27)
-    linearize_kernel<27><<<grid, block, 0, st>>>(L);
-  else
-    linearize_kernel<1><<<grid, block, 0, st>>>(L);
+  if (L.neighbours == 27) {
+    linearize_simple_kernel<27><<<grid, kSimpleThreads, 0, st>>>(L);
+  } else if (variant == 1) {
+    linearize_simple_kernel<1><<<grid, kSimpleThreads, 0, st>>>(L);
+  } else {
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+      VGICP_CUDA_TRY(cudaFuncSetAttribute(tma::linearize_tma_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(tma::Smem)));
+      attr_set[dev] = true;
+    }
+    tma::linearize_tma_kernel<<<grid, tma::kThreads, sizeof(tma::Smem), st>>>(L);
+  }
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   if (L.ev_stop) VGICP_CUDA_TRY(cudaEventRecord(L.ev_stop, st));
   return VGICP_OK;
 }
 
-int launch_reduce(const double* partials, const int32_t* item_off, int32_t n_items_single,
-                  int64_t n_pairs, double* out, int64_t* inliers, cudaStream_t st) {
+int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
+                  int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
+                  cudaStream_t st) {
   if (n_pairs <= 0) return VGICP_OK;
   const int warps = 8;
   const int64_t blocks = (n_pairs + warps - 1) / warps;
-  reduce_kernel<<<(unsigned)blocks, warps * 32, 0, st>>>(partials, item_off, n_items_single,
-                                                         n_pairs, out, inliers);
+  reduce_kernel<<<(unsigned)blocks, warps * 32, 0, st>>>(partials, span, n_items_single, n_pairs,
+                                                         status, out, inliers);
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return VGICP_OK;

@@ -265,3 +265,40 @@ def test_pose_validation(dev):
         api.linearize(vm, cu(sp), cu(sc), scaled)
     with pytest.raises(VGICPError):
         api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 1]], T[None])
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_kernel_variants_match_oracle(dev, variant):
+    tp, tc, sp, sc, T, r = cases.room()
+    vm = api.VoxelMap.build(cu(tp), cu(tc), r)
+    lin = api.linearize(vm, cu(sp), cu(sc), T, corr=True, variant=variant)
+    ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, debug=True)
+    assert np.array_equal(lin.corr.cpu().numpy().astype(np.int64), ref.corr)
+    check_factor(lin.out, lin.inliers, ref, f"variant {variant}")
+    bat = api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 0]], T[None], variant=variant,
+                                tile=1000)
+    check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}")
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_map_as_source(dev, variant):
+    """A map's own (voxel-grouped) cloud as the source gives the same factor as the
+    original cloud, within tolerance, and matches the oracle."""
+    w = cases.workload_with_knn_covs("outdoor", seed=33, n_submaps=10, neighbours=3)
+    C = len(w.clouds.offsets) - 1
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    srcs = [(pts[w.clouds.offsets[c]:w.clouds.offsets[c + 1]],
+             covs[w.clouds.offsets[c]:w.clouds.offsets[c + 1]]) for c in range(C)]
+    a = api.linearize_batched(maps, srcs, w.pairs, w.poses, variant=variant)
+    b = api.linearize_batched(maps, maps, w.pairs, w.poses, variant=variant)
+    assert torch.equal(a.inliers, b.inliers)
+    omaps = {}
+    for p, (j, i) in enumerate(w.pairs[:8]):
+        if j not in omaps:
+            tp, tc = w.clouds.cloud(j)
+            omaps[j] = oracle.build_voxelmap(tp, tc, w.resolution)
+        sp, sc = w.clouds.cloud(i)
+        ref = oracle.linearize(omaps[j], sp, sc, w.poses[p], nthreads=0)
+        check_factor(b.out[p], b.inliers[p], ref, f"pair {p}")
