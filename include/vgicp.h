@@ -151,6 +151,28 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
                     int64_t n_src, const double* T_target_source, double* out, int64_t* inliers,
                     const vgicp_lin_opts* opts, vgicp_stream_t stream);
 
+/* vgicp_linearize without any device allocation (the paper has no counterpart:
+ * this serves callers that may not allocate device memory once running, such as
+ * a real-time loop whose GPU memory is fixed at start-up, or a plugin handed a
+ * stream by a framework that forbids allocations on it).  Same arguments and
+ * results as vgicp_linearize.  Its scratch (per-item partial sums and a status
+ * word) is one fixed array in device memory that exists on every GPU that loads
+ * the library, until the process exits, so no call allocates or frees.
+ *   - Limit: at most 4096 work items per call, i.e. n_src <= 4096 * item size
+ *     (automatic item size up to 16384 points: n_src up to 67,108,864); larger
+ *     calls return VGICP_ERR_INVALID_ARG with a message and launch nothing.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the array and it keeps the last call's contents (the
+ *     status word is cleared by each call).  Calls whose kernels overlap on the
+ *     GPU (different streams without ordering, or concurrent host threads) race
+ *     on it and give wrong results: serialize them, e.g. on one stream. */
+int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_points,
+                            const float* src_covs, int64_t n_src, const double* T_target_source,
+                            double* out, int64_t* inliers, const vgicp_lin_opts* opts,
+                            vgicp_stream_t stream);
+
 /* A source cloud for batched calls (device pointers), or a voxel map whose own
  * cloud is the source: when `map` is non-null, points/covs/n are ignored and the
  * map's cloud is read in the voxel-grouped order its build produced (points of

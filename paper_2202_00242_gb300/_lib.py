@@ -44,6 +44,8 @@ SIGNATURES = {
     "vgicp_voxelmap_info": (ctypes.c_int, [P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "vgicp_voxelmap_export": (ctypes.c_int, [P, P, i64, P, P, P, P]),
     "vgicp_linearize": (ctypes.c_int, [P, P, P, i64, P, P, P, ctypes.POINTER(LinOpts), P]),
+    "vgicp_linearize_noalloc": (ctypes.c_int, [P, P, P, i64, P, P, P, ctypes.POINTER(LinOpts),
+                                               P]),
     "vgicp_linearize_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
                                                P, i64, P, P, P, ctypes.POINTER(LinOpts), P]),
 }

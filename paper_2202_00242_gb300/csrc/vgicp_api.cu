@@ -596,3 +596,109 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Single-factor linearization without any device allocation.
+//
+// Some callers cannot allocate device memory once they are running: a
+// real-time front-end that sizes its whole GPU footprint at start-up and must
+// not take the allocator's locks or latency inside its control loop, or a host
+// framework that hands a plugin a stream and forbids allocations on it.  This
+// entry point serves them.  It keeps the per-item partial sums and the status
+// word in one fixed array in device memory, declared below, so it calls no
+// cudaMalloc / cudaFree of any kind.  The array is created when the library is
+// loaded and every GPU that loads the library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int32_t kNoAllocMaxItems = 4096;  // work items per call (1 MiB of partials)
+// partials: kNoAllocMaxItems x kPartialStride doubles, then 32 doubles of which
+// the first 4 bytes are the status word
+static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxItems + 1) * kPartialStride];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device.  The array's name
+// in host code only stands for the symbol; the address must be asked for with
+// that device current.  Done once per device, on its first call.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  VGICP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(VGICP_ERR_INVALID_ARG, "device index above 63");
+  std::lock_guard<std::mutex> g(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return VGICP_OK;
+}
+
+}  // namespace
+
+extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_points,
+                                       const float* src_covs, int64_t n_src,
+                                       const double* T_target_source, double* out,
+                                       int64_t* inliers, const vgicp_lin_opts* opts,
+                                       vgicp_stream_t stream) {
+  g_error.clear();
+  if (!map || !out || !inliers || !T_target_source)
+    return set_error(VGICP_ERR_INVALID_ARG, "null map, output or pose");
+  int rc = check_cloud(src_points, src_covs, n_src, "source cloud");
+  if (rc) return rc;
+  if (!finite_pose(T_target_source))
+    return set_error(VGICP_ERR_INVALID_ARG, "pose must be a finite rigid transform");
+  const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
+  if (neighbours != 1 && neighbours != 27)
+    return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
+  if (opts && (opts->variant < 0 || opts->variant > 2))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  int item = opts && opts->tile > 0 ? opts->tile : 0;
+  if (item == 0) {
+    const int64_t target_items =
+        linearize_grid(neighbours, opts && opts->variant ? opts->variant : default_variant());
+    int64_t t = (n_src + target_items - 1) / std::max<int64_t>(target_items, 1);
+    t = std::max<int64_t>(256, std::min<int64_t>(default_item_size(), (t + 255) / 256 * 256));
+    item = (int)t;
+  }
+  const int64_t n_items = (n_src + item - 1) / item;
+  if (n_items > kNoAllocMaxItems)
+    return set_error(VGICP_ERR_INVALID_ARG,
+                     "vgicp_linearize_noalloc: " + std::to_string(n_items) +
+                         " work items exceed its fixed scratch of " +
+                         std::to_string(kNoAllocMaxItems) +
+                         " (n_src / item size must be at most that; raise opts->tile or use "
+                         "vgicp_linearize)");
+  double* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  LinLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.items = nullptr;
+  L.n_items = (int32_t)n_items;
+  L.item_size = item;
+  L.single = make_pair_desc(T_target_source, 0, 0);
+  L.single_map = make_map_desc(map);
+  L.single_src = SrcDesc{src_points, src_covs, n_src};
+  L.corr_out = opts ? opts->corr_out : nullptr;
+  L.qkey_out = opts ? opts->qkey_out : nullptr;
+  L.neighbours = neighbours;
+  L.variant = opts ? opts->variant : 0;
+  L.grid = opts ? opts->grid : 0;
+  L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
+  L.ev_stop = opts ? static_cast<cudaEvent_t>(opts->kernel_stop) : nullptr;
+  L.partials = scratch;
+  L.status = reinterpret_cast<int32_t*>(scratch + (size_t)kNoAllocMaxItems * kPartialStride);
+  // the array keeps the previous call's contents: the status word must start at
+  // zero; every partial the reduction reads is written by this call
+  VGICP_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(int32_t), st));
+  rc = launch_linearize(L, st);
+  if (rc == VGICP_OK)
+    rc = launch_reduce(L.partials, nullptr, (int32_t)n_items, 1, L.status, out, inliers, st);
+  return rc;
+}
