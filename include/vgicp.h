@@ -134,7 +134,8 @@ typedef struct {
   int32_t tile;       /* source points per work item; 0 = automatic */
   int32_t grid;       /* CTAs of the persistent launch; 0 = automatic */
   int32_t variant;    /* 1-neighbour kernel: 0 = automatic, 1 = one point per thread,
-                         2 = shared-memory staged (bulk asynchronous copies) */
+                         2 = shared-memory staged (bulk asynchronous copies),
+                         3 = per-warp software pipeline with hit compaction */
   int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
                          point's own voxel (first-appearance numbering) or -1 */
   int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
@@ -197,6 +198,47 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
                             int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                             const double* poses, double* out, int64_t* inliers,
                             const vgicp_lin_opts* opts, vgicp_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Plans: a fixed factor set linearized at every optimizer iteration          */
+/* (Sec. III-A re-linearizes each factor per iteration; Sec. III-F links every */
+/* overlapping submap pair).  The work list is built once, the launch shape   */
+/* can be chosen by timing candidates (autotune), and one linearization is    */
+/* captured in a CUDA graph replayed with new poses.                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct vgicp_plan vgicp_plan;
+
+/* Same factor description as vgicp_linearize_batched (maps, sources, pairs are
+ * host arrays; sources may reference maps).  opts: neighbours, tile (points
+ * per work item, 0 = default 16384, else >= 2048), variant, grid.  Allocates
+ * the plan's device and pinned host buffers.  The maps and source clouds must
+ * outlive the plan. */
+int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                      int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                      const vgicp_lin_opts* opts, vgicp_stream_t stream, vgicp_plan** out);
+
+/* Synchronizes.  Times each kernel variant (1-neighbour: 1, 2, 3) with work items
+ * of 4096, 8192, 16384 and 32768 points on these poses (host, n_pairs x 16) and
+ * keeps the fastest; results then depend (within float32 rounding) on that
+ * choice, and are deterministic for it. */
+int vgicp_plan_autotune(vgicp_plan* plan, const double* poses, vgicp_stream_t stream);
+
+/* Linearize all factors at poses (host, n_pairs x 16 doubles, read during the
+ * call).  out: device n_pairs x 43, inliers: device n_pairs (either may be NULL;
+ * results are copied there after the graph).  kernel_start/kernel_stop:
+ * optional cudaEvent_t recorded on the stream around the graph launch (status
+ * reset, linearize kernel, per-pair reduction).  The first call captures the
+ * graph. */
+int vgicp_plan_execute(vgicp_plan* plan, const double* poses, double* out, int64_t* inliers,
+                       void* kernel_start, void* kernel_stop, vgicp_stream_t stream);
+
+/* Current launch shape: kernel variant, points per work item, CTAs, work items. */
+int vgicp_plan_info(const vgicp_plan* plan, int32_t* variant, int32_t* item_points,
+                    int32_t* grid, int64_t* n_items);
+
+/* Waits for the device to finish using the plan, then releases it. */
+int vgicp_plan_destroy(vgicp_plan* plan);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,13 @@ SIGNATURES = {
                                                P]),
     "vgicp_linearize_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
                                                P, i64, P, P, P, ctypes.POINTER(LinOpts), P]),
+    "vgicp_plan_create": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32, P,
+                                         i64, ctypes.POINTER(LinOpts), P, ctypes.POINTER(P)]),
+    "vgicp_plan_autotune": (ctypes.c_int, [P, P, P]),
+    "vgicp_plan_execute": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "vgicp_plan_info": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+    "vgicp_plan_destroy": (ctypes.c_int, [P]),
 }
 
 _lib = None

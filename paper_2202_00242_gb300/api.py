@@ -234,3 +234,69 @@ def linearize_batched(maps: list[VoxelMap], sources, pairs, poses, neighbours=1,
                                               ctypes.c_void_p(inliers.data_ptr()),
                                               ctypes.byref(opts), _stream_ptr(stream)))
     return Linearization(out, inliers)
+
+
+class Plan:
+    """A fixed factor set linearized repeatedly (one CUDA graph per iteration).
+
+    maps, sources and pairs as in ``linearize_batched``; ``tile`` = points per
+    work item (0: default), ``variant`` = 1-neighbour kernel (0: default).
+    ``autotune(poses)`` times the kernel variants and item sizes and keeps the
+    fastest; ``execute(poses)`` linearizes all factors.
+    """
+
+    def __init__(self, maps, sources, pairs, neighbours=1, tile=0, variant=0, grid=0,
+                 stream=None):
+        self._lib = _lib.load()
+        self.pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.n_pairs = self.pairs.shape[0]
+        self._refs = (list(maps), list(sources))
+        clouds = make_clouds(sources)
+        arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+        opts = LinOpts(int(neighbours), int(tile), int(grid), int(variant), None, None, None,
+                       None)
+        h = ctypes.c_void_p()
+        check(self._lib.vgicp_plan_create(arr, len(maps), clouds, len(sources),
+                                          self.pairs.ctypes.data_as(ctypes.c_void_p),
+                                          self.n_pairs, ctypes.byref(opts), _stream_ptr(stream),
+                                          ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def autotune(self, poses, stream=None):
+        poses = _pose_array(poses, self.n_pairs)
+        check(self._lib.vgicp_plan_autotune(self._h, poses.ctypes.data_as(ctypes.c_void_p),
+                                            _stream_ptr(stream)))
+        return self.info()
+
+    def execute(self, poses, out=None, inliers=None, events=None, stream=None) -> Linearization:
+        poses = _pose_array(poses, self.n_pairs)
+        if out is None:
+            out = torch.empty((self.n_pairs, RESULT_SIZE), dtype=torch.float64, device=self.device)
+        if inliers is None:
+            inliers = torch.empty(self.n_pairs, dtype=torch.int64, device=self.device)
+        ev0 = ctypes.c_void_p(events[0].cuda_event) if events is not None else None
+        ev1 = ctypes.c_void_p(events[1].cuda_event) if events is not None else None
+        check(self._lib.vgicp_plan_execute(self._h, poses.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(inliers.data_ptr()), ev0, ev1,
+                                           _stream_ptr(stream)))
+        return Linearization(out, inliers)
+
+    def info(self) -> dict:
+        v, it, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        n = ctypes.c_int64()
+        check(self._lib.vgicp_plan_info(self._h, ctypes.byref(v), ctypes.byref(it), ctypes.byref(g),
+                                        ctypes.byref(n)))
+        return {"variant": v.value, "item_points": it.value, "grid": g.value, "items": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vgicp_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

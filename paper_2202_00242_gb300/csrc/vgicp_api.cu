@@ -27,6 +27,8 @@ uint32_t next_pow2(uint64_t x) {
   return (uint32_t)p;
 }
 
+}  // namespace
+
 bool finite_pose(const double* T) {
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(T[i])) return false;
@@ -89,6 +91,8 @@ int check_cloud(const float* pts, const float* covs, int64_t n, const char* what
                      std::string(what) + ": points must be 4-byte and covs 8-byte aligned");
   return VGICP_OK;
 }
+
+namespace {
 
 int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
                const vgicp_map_opts* opts, cudaStream_t st, MapSet** out) {
@@ -480,8 +484,8 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 2))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -654,8 +658,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 2))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =

@@ -156,42 +156,133 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
   }
 }
 
-__global__ void finalize_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
-                                const float* __restrict__ pts, const float* __restrict__ covs,
-                                const uint32_t* __restrict__ vcount,
-                                const uint32_t* __restrict__ voff, uint32_t* __restrict__ plist,
-                                float4* __restrict__ recs) {
-  const int64_t V = *n_vox;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = vcount[v];
-    uint32_t* L = plist + voff[v];
-    // ascending point index (lists are short: a voxel holds a handful of points)
-    for (uint32_t a = 1; a < c; ++a) {
-      uint32_t x = L[a];
-      int b = (int)a - 1;
-      while (b >= 0 && L[b] > x) {
-        L[b + 1] = L[b];
-        --b;
+// Per-voxel binary64 sums in ascending point index.  A CTA takes 256 consecutive
+// voxels, whose point lists are one contiguous segment of plist: the segment is
+// loaded into shared memory (coalesced), each thread sorts its voxel's short
+// list there, the sorted segment is written back (the grouping step reads it),
+// and the sums gather the points four at a time.  Segments longer than the
+// staging buffer fall back to sorting in global memory.
+constexpr int kFinThreads = 256;
+constexpr int kFinStage = 6144;  // indices staged per CTA
+
+__device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
+  for (uint32_t a = 1; a < c; ++a) {
+    const uint32_t x = L[a];
+    int b = (int)a - 1;
+    while (b >= 0 && L[b] > x) {
+      L[b + 1] = L[b];
+      --b;
+    }
+    L[b + 1] = x;
+  }
+}
+
+// Exact sum of float32 values in a double-float (hi + lo) accumulator: TwoSum
+// (Knuth; Moeller) keeps hi + lo equal to the running sum as long as the one
+// rounding step, lo + e, is exact; that is checked (its own TwoSum error must be
+// 0) and reported through `exact`.  While exact, hi + lo is the exact sum, equal
+// to the binary64 sum in any order, so no ordering is needed for it.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v, bool& exact) {
+  float t, e, u, e2;
+  two_sum(hi, v, t, e);
+  two_sum(lo, e, u, e2);
+  exact = exact && (e2 == 0.0f);
+  two_sum(t, u, hi, lo);
+}
+
+// Correctly rounded binary64 quotient s / n from the rounded reciprocal and one
+// correction step (Markstein's theorem: with y = RN(1/n) and q = RN(s*y), the
+// residual r = s - q*n is exact under FMA and RN(q + r*y) = RN(s/n)).
+__device__ __forceinline__ double div_rn(double s, double n, double y) {
+  const double q = __dmul_rn(s, y);
+  const double r = __fma_rn(-q, n, s);
+  return __fma_rn(r, y, q);
+}
+
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(
+    int64_t n_max, const uint32_t* __restrict__ n_vox, const float* __restrict__ pts,
+    const float* __restrict__ covs, const uint32_t* __restrict__ vcount,
+    const uint32_t* __restrict__ voff, uint32_t* __restrict__ plist, float4* __restrict__ recs,
+    const uint32_t* __restrict__ vrank, const uint32_t* __restrict__ goff,
+    float* __restrict__ gpts, float* __restrict__ gcovs) {
+  __shared__ uint32_t stage[kFinStage];
+  const int64_t V = min((int64_t)*n_vox, n_max);
+  for (int64_t v0 = (int64_t)blockIdx.x * kFinThreads; v0 < V; v0 += (int64_t)gridDim.x * kFinThreads) {
+    const int64_t v1 = min(V, v0 + kFinThreads);
+    const uint32_t seg0 = voff[v0];
+    const uint32_t seg1 = voff[v1 - 1] + vcount[v1 - 1];
+    const bool staged = seg1 - seg0 <= (uint32_t)kFinStage;
+    const int64_t v = v0 + threadIdx.x;
+    const bool mine = v < v1;
+    const uint32_t c = mine ? vcount[v] : 0u;
+    const uint32_t o = mine ? voff[v] : 0u;
+    if (staged) {
+      for (uint32_t i = threadIdx.x; i < seg1 - seg0; i += kFinThreads) stage[i] = plist[seg0 + i];
+      __syncthreads();
+      if (mine) insertion_sort(stage + (o - seg0), c);
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < seg1 - seg0; i += kFinThreads) plist[seg0 + i] = stage[i];
+    } else if (mine) {
+      insertion_sort(plist + o, c);
+    }
+    if (mine) {
+      const uint32_t* Lst = staged ? stage + (o - seg0) : plist + o;
+      const int64_t dst0 = goff[vrank[v]];
+      float hi[9], lo[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) hi[k] = lo[k] = 0.0f;
+      bool exact = true;
+      for (uint32_t a = 0; a < c; ++a) {
+        const int64_t j = Lst[a];
+        float f[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f[k] = __ldg(pts + 3 * j + k);
+        const float2* cv = reinterpret_cast<const float2*>(covs + 6 * j);
+        const float2 c0 = __ldg(cv), c1 = __ldg(cv + 1), c2 = __ldg(cv + 2);
+        f[3] = c0.x; f[4] = c0.y; f[5] = c1.x; f[6] = c1.y; f[7] = c2.x; f[8] = c2.y;
+        // the voxel-grouped, spatially ordered copy of the cloud
+        const int64_t d = dst0 + a;
+        gpts[3 * d + 0] = f[0];
+        gpts[3 * d + 1] = f[1];
+        gpts[3 * d + 2] = f[2];
+        float2* gc = reinterpret_cast<float2*>(gcovs + 6 * d);
+        gc[0] = c0;
+        gc[1] = c1;
+        gc[2] = c2;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) df_add(hi[k], lo[k], f[k], exact);
       }
-      L[b + 1] = x;
-    }
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (uint32_t a = 0; a < c; ++a) {
-      const int64_t j = L[a];
-      s[0] = __dadd_rn(s[0], (double)__ldg(pts + 3 * j + 0));
-      s[1] = __dadd_rn(s[1], (double)__ldg(pts + 3 * j + 1));
-      s[2] = __dadd_rn(s[2], (double)__ldg(pts + 3 * j + 2));
+      double s[9];
+      if (exact) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) s[3 + k] = __dadd_rn(s[3 + k], (double)__ldg(covs + 6 * j + k));
-    }
-    const double N = (double)c;
-    float f[9];
+        for (int k = 0; k < 9; ++k) s[k] = __dadd_rn((double)hi[k], (double)lo[k]);  // exact
+      } else {
+        // binary64 sum in ascending point index (rare: large dynamic range)
 #pragma unroll
-    for (int k = 0; k < 9; ++k) f[k] = __double2float_rn(__ddiv_rn(s[k], N));
-    recs[3 * v + 0] = make_float4(f[0], f[1], f[2], __uint_as_float(c));
-    recs[3 * v + 1] = make_float4(f[3], f[4], f[5], f[6]);
-    recs[3 * v + 2] = make_float4(f[7], f[8], 0.0f, 0.0f);
+        for (int k = 0; k < 9; ++k) s[k] = 0.0;
+        for (uint32_t a = 0; a < c; ++a) {
+          const int64_t j = Lst[a];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s[k] = __dadd_rn(s[k], (double)__ldg(pts + 3 * j + k));
+#pragma unroll
+          for (int k = 0; k < 6; ++k) s[3 + k] = __dadd_rn(s[3 + k], (double)__ldg(covs + 6 * j + k));
+        }
+      }
+      const double N = (double)c;
+      const double y = __drcp_rn(N);
+      float r[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) r[k] = __double2float_rn(div_rn(s[k], N, y));
+      recs[3 * v + 0] = make_float4(r[0], r[1], r[2], __uint_as_float(c));
+      recs[3 * v + 1] = make_float4(r[3], r[4], r[5], r[6]);
+      recs[3 * v + 2] = make_float4(r[7], r[8], 0.0f, 0.0f);
+    }
+    __syncthreads();  // the stage is reused by the next batch
   }
 }
 
@@ -260,31 +351,6 @@ __global__ void rank_counts_kernel(int64_t n_max, const uint32_t* __restrict__ n
     gcount[vrank[v]] = vcount[v];
 }
 
-// The clouds grouped by voxel, voxels in Morton order, points of a voxel in
-// ascending index: point j of voxel v (at list position pos) goes to
-// goff[vrank[v]] + (pos - voff[v]).
-__global__ void group_kernel(int64_t n_total, const uint32_t* __restrict__ n_valid,
-                             const uint32_t* __restrict__ plist,
-                             const uint32_t* __restrict__ pt_slot, const Slot* __restrict__ slots,
-                             const uint32_t* __restrict__ voff, const uint32_t* __restrict__ vrank,
-                             const uint32_t* __restrict__ goff, const float* __restrict__ pts,
-                             const float* __restrict__ covs, float* __restrict__ gpts,
-                             float* __restrict__ gcovs) {
-  const int64_t n = min(n_total, (int64_t)*n_valid);  // only positions holding a point
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = plist[p];
-    const uint32_t v = slots[pt_slot[j]].vid;
-    const int64_t pos = (int64_t)goff[vrank[v]] + (p - (int64_t)voff[v]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) gpts[3 * pos + k] = __ldg(pts + 3 * j + k);
-    const float2* c = reinterpret_cast<const float2*>(covs + 6 * j);
-    float2* g = reinterpret_cast<float2*>(gcovs + 6 * pos);
-    g[0] = __ldg(c);
-    g[1] = __ldg(c + 1);
-    g[2] = __ldg(c + 2);
-  }
-}
 
 __device__ __forceinline__ uint32_t lookup_capacity(uint32_t nvox) {
   uint32_t c = 16;
@@ -509,20 +575,9 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   if (rc != VGICP_OK) return rc;
   scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_voff, s->d_vfill,
                                          s->d_plist);
-  finalize_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
-                                          s->d_voff, s->d_plist, s->d_recs);
-  int64_t max_cap = 16;
-  for (int32_t m = 0; m < s->n_maps; ++m)
-    max_cap = std::max<int64_t>(max_cap, (m + 1 < s->n_maps ? s->vslot_base[m + 1] : s->vcap_total) -
-                                             s->vslot_base[m]);
-  const unsigned gx = (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
-  vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
-                                                             s->d_vslots, s->d_vmask);
-  vslot_insert_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, s->n_maps, s->d_vbase,
-                                              s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
-                                              s->max_probe, s->d_vslots, s->d_status);
-  // voxel-grouped, spatially ordered copy of the clouds (the sources of map-sourced
-  // factors): d_flag and d_vfill are free scratch at this point
+  // Morton order of the voxels (chunks of a map) and the grouped offsets, then the
+  // per-voxel sums, which also write the voxel-grouped copy of the clouds;
+  // d_flag and d_vfill are free scratch at this point
   uint32_t* vrank = s->d_flag;
   uint32_t* gcount = s->d_vfill;
   static bool sort_attr = false;
@@ -538,13 +593,23 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   VGICP_CUDA_TRY(cudaGetLastError());
   rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp, nullptr, st);
   if (rc != VGICP_OK) return rc;
-  group_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_valid, s->d_plist, s->d_pt_slot, s->d_slots,
-                                       s->d_voff, vrank, s->d_goff, points, covs, s->d_gpts,
-                                       s->d_gcovs);
+  finalize_kernel<<<g, kFinThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
+                                             s->d_voff, s->d_plist, s->d_recs, vrank, s->d_goff,
+                                             s->d_gpts, s->d_gcovs);
+  int64_t max_cap = 16;
+  for (int32_t m = 0; m < s->n_maps; ++m)
+    max_cap = std::max<int64_t>(max_cap, (m + 1 < s->n_maps ? s->vslot_base[m + 1] : s->vcap_total) -
+                                             s->vslot_base[m]);
+  const unsigned gx = (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
+  vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
+                                                             s->d_vslots, s->d_vmask);
+  vslot_insert_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, s->n_maps, s->d_vbase,
+                                              s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
+                                              s->max_probe, s->d_vslots, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, first, assign, vbase, scatter, finalize, vslot init/insert, sort, rank counts,
-  // group (+ init: 1)
-  count_launches(11);
+  // insert, first, assign, vbase, scatter, sort, rank counts, finalize, vslot init/insert
+  // (+ init: 1)
+  count_launches(10);
   return VGICP_OK;
 }
 

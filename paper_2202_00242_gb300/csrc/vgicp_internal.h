@@ -125,6 +125,12 @@ int launch_reduce(const double* partials, const int2* span, int32_t n_items_sing
 
 int device_sm_count();
 
+// Shared host helpers (vgicp_api.cu).
+bool finite_pose(const double* T);  // finite rigid transform, last row 0 0 0 1
+PairDesc make_pair_desc(const double* T, int32_t map, int32_t src);
+MapDesc make_map_desc(const vgicp_map* m);
+int check_cloud(const float* pts, const float* covs, int64_t n, const char* what);
+
 // Count of kernels launched by the library (vgicp_launch_count).
 void count_launches(int n);
 

@@ -714,6 +714,213 @@ __global__ void __launch_bounds__(kSimpleThreads, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined per-warp kernel (1 neighbour).  Each warp walks 32-point chunks of
+// the CTA's work item with a software pipeline:
+//   chunk k+2: point data loads in flight (registers)
+//   chunk k+1: key computed, first probe of its slot (two 256-bit loads) in flight
+//   chunk k  : probes resolved; hits pushed to a per-warp queue in shared memory
+//              (point and voxel Gaussian, 80 B per entry)
+// and whenever 32 hits are queued, the warp evaluates them with every lane busy.
+// The lookups and the stream are both a full iteration ahead of their use.
+// ---------------------------------------------------------------------------
+namespace pipe {
+constexpr int kWarps = 6;
+constexpr int kThreads = kWarps * 32;
+constexpr int kQueue = 64;  // entries per warp (< 32 after a drain + at most 32 pushed)
+
+struct Chunk {  // one point per lane
+  float x, y, z;
+  float c[6];
+  bool valid;
+};
+
+__device__ __forceinline__ void load_chunk(const SrcDesc& sd, int64_t p, bool valid, Chunk& ch) {
+  ch.valid = valid;
+  if (valid) {
+    const float* pt = sd.pts + 3 * p;
+    ch.x = __ldg(pt);
+    ch.y = __ldg(pt + 1);
+    ch.z = __ldg(pt + 2);
+    const float2* cv = reinterpret_cast<const float2*>(sd.covs + 6 * p);
+    const float2 a = __ldg(cv), b = __ldg(cv + 1), c = __ldg(cv + 2);
+    ch.c[0] = a.x; ch.c[1] = a.y; ch.c[2] = b.x; ch.c[3] = b.y; ch.c[4] = c.x; ch.c[5] = c.y;
+  } else {
+    ch.x = ch.y = ch.z = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ch.c[k] = 0.f;
+  }
+}
+
+struct Probe {
+  unsigned long long key;
+  uint32_t h;
+  int kx, ky, kz;
+  bool live;
+  uint32_t a[8], b[8];
+};
+
+__device__ __forceinline__ void start_probe(const Pose32& P, const PairDesc* pd, const MapDesc& md,
+                                            uint32_t mask, uint64_t pol, const Chunk& ch,
+                                            Probe& pr) {
+  pr.kx = pr.ky = pr.kz = kKeyMin - 1;
+  pr.live = false;
+  if (ch.valid) {
+    const float qx = fmaf(P.R[0], ch.x, fmaf(P.R[1], ch.y, fmaf(P.R[2], ch.z, P.t[0])));
+    const float qy = fmaf(P.R[3], ch.x, fmaf(P.R[4], ch.y, fmaf(P.R[5], ch.z, P.t[1])));
+    const float qz = fmaf(P.R[6], ch.x, fmaf(P.R[7], ch.y, fmaf(P.R[8], ch.z, P.t[2])));
+    source_key(P, pd, md, ch.x, ch.y, ch.z, qx, qy, qz, pr.kx, pr.ky, pr.kz);
+    pr.live = key_in_range(pr.kx) && key_in_range(pr.ky) && key_in_range(pr.kz);
+  }
+  pr.key = pr.live ? pack_key(pr.kx, pr.ky, pr.kz) : kEmptyKey;
+  pr.h = hash_key(pr.kx, pr.ky, pr.kz) & mask;
+  if (pr.live) {
+    ld_v8(md.vslots + pr.h, pol, pr.a);
+    ld_v8(reinterpret_cast<const char*>(md.vslots + pr.h) + 32, pol, pr.b);
+  } else {
+    pr.a[0] = pr.a[1] = 0xFFFFFFFFu;
+  }
+}
+
+// Resolve a probe (further probes are rare); returns the global voxel id or -1.
+__device__ __forceinline__ int finish_probe(const MapDesc& md, uint32_t mask, uint64_t pol,
+                                            Probe& pr) {
+  if (!pr.live) return -1;
+  unsigned long long t = slot_key(pr.a);
+  uint32_t hh = pr.h;
+  for (int p = 1; t != pr.key && t != kEmptyKey && p < md.max_probe; ++p) {
+    hh = (hh + 1) & mask;
+    ld_v8(md.vslots + hh, pol, pr.a);
+    ld_v8(reinterpret_cast<const char*>(md.vslots + hh) + 32, pol, pr.b);
+    t = slot_key(pr.a);
+  }
+  return t == pr.key ? (int)pr.a[2] : -1;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __grid_constant__ LinLaunch L) {
+  __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
+  __shared__ float red[kWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t pol = policy_evict_last_l();
+  float4* Q = queue[warp];
+
+  for (int it = blockIdx.x; it < L.n_items; it += gridDim.x) {
+    int pair, b, e;
+    tma::item_bounds(L, it, pair, b, e);
+    const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+    Pose32 P;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
+    P.t[0] = pd->t[0];
+    P.t[1] = pd->t[1];
+    P.t[2] = pd->t[2];
+    P.tmax = pd->tmax;
+    const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
+    const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
+    const uint32_t mask = *md.vmask;
+    uint32_t vbase = 0;
+    if (L.corr_out) vbase = *md.vbase;
+
+    float acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+    int qn = 0;  // queued hits (warp-uniform)
+
+    const int nchunks = (e - b + 31) >> 5;
+    // chunk sequence of this warp: warp, warp + kWarps, ...
+    auto chunk_point = [&](int j) -> int64_t { return (int64_t)b + 32 * (int64_t)(warp + j * kWarps) + lane; };
+    auto chunk_exists = [&](int j) -> bool { return warp + j * kWarps < nchunks; };
+
+    Chunk nxt, cur, pnd;
+    Probe pcur, ppnd;
+    load_chunk(sd, chunk_point(0), chunk_exists(0) && chunk_point(0) < e, cur);
+    load_chunk(sd, chunk_point(1), chunk_exists(1) && chunk_point(1) < e, nxt);
+    start_probe(P, pd, md, mask, pol, cur, pcur);
+
+    for (int j = 0; chunk_exists(j); ++j) {
+      // rotate: chunk j is resolved now; chunk j+1 gets its probe; chunk j+2 loads
+      pnd = cur;
+      ppnd = pcur;
+      cur = nxt;
+      load_chunk(sd, chunk_point(j + 2), chunk_exists(j + 2) && chunk_point(j + 2) < e, nxt);
+      start_probe(P, pd, md, mask, pol, cur, pcur);
+
+      const int vid = finish_probe(md, mask, pol, ppnd);
+      if (L.corr_out || L.qkey_out) {
+        const int64_t p = chunk_point(j);
+        if (pnd.valid) {
+          if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+          if (L.qkey_out) {
+            L.qkey_out[3 * p + 0] = ppnd.kx;
+            L.qkey_out[3 * p + 1] = ppnd.ky;
+            L.qkey_out[3 * p + 2] = ppnd.kz;
+          }
+        }
+      }
+      const bool hit = vid >= 0;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+      if (hit) {
+        float4* E = Q + 5 * (qn + __popc(m & lt_mask));
+        E[0] = make_float4(pnd.x, pnd.y, pnd.z, pnd.c[0]);
+        E[1] = make_float4(pnd.c[1], pnd.c[2], pnd.c[3], pnd.c[4]);
+        E[2] = make_float4(pnd.c[5], __uint_as_float(ppnd.a[4]), __uint_as_float(ppnd.a[5]),
+                           __uint_as_float(ppnd.a[6]));
+        E[3] = make_float4(__uint_as_float(ppnd.b[0]), __uint_as_float(ppnd.b[1]),
+                           __uint_as_float(ppnd.b[2]), __uint_as_float(ppnd.b[3]));
+        E[4] = make_float4(__uint_as_float(ppnd.b[4]), __uint_as_float(ppnd.b[5]), 0.f, 0.f);
+      }
+      if (lane == 0) acc[28] += (float)__popc(m);
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
+        const float4* E = Q + 5 * (qn - 32 + lane);
+        const float4 e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4];
+        const float c[6] = {e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
+        const float qx = fmaf(P.R[0], e0.x, fmaf(P.R[1], e0.y, fmaf(P.R[2], e0.z, P.t[0])));
+        const float qy = fmaf(P.R[3], e0.x, fmaf(P.R[4], e0.y, fmaf(P.R[5], e0.z, P.t[1])));
+        const float qz = fmaf(P.R[6], e0.x, fmaf(P.R[7], e0.y, fmaf(P.R[8], e0.z, P.t[2])));
+        add_term(acc, P, e0.x, e0.y, e0.z, c, qx, qy, qz, make_float4(e2.y, e2.z, e2.w, 0.f),
+                 e3, make_float4(e4.x, e4.y, 0.f, 0.f));
+        acc[28] -= 1.0f;  // add_term counts an inlier; hits were counted at the push
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    // drain the partially filled queue
+    if (lane < qn) {
+      const float4* E = Q + 5 * lane;
+      const float4 e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4];
+      const float c[6] = {e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
+      const float qx = fmaf(P.R[0], e0.x, fmaf(P.R[1], e0.y, fmaf(P.R[2], e0.z, P.t[0])));
+      const float qy = fmaf(P.R[3], e0.x, fmaf(P.R[4], e0.y, fmaf(P.R[5], e0.z, P.t[1])));
+      const float qz = fmaf(P.R[6], e0.x, fmaf(P.R[7], e0.y, fmaf(P.R[8], e0.z, P.t[2])));
+      add_term(acc, P, e0.x, e0.y, e0.z, c, qx, qy, qz, make_float4(e2.y, e2.z, e2.w, 0.f), e3,
+               make_float4(e4.x, e4.y, 0.f, 0.f));
+      acc[28] -= 1.0f;
+    }
+    __syncwarp();
+
+    // reduce: warp reduce-scatter, then binary64 across warps
+    tma::rs_step<16>(acc, lane);
+    tma::rs_step<8>(acc, lane);
+    tma::rs_step<4>(acc, lane);
+    tma::rs_step<2>(acc, lane);
+    tma::rs_step<1>(acc, lane);
+    red[warp][lane] = acc[0];
+    __syncthreads();
+    if (warp == 0 && lane < kAcc) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += (double)red[w][lane];
+      L.partials[(int64_t)it * kPartialStride + lane] = t;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pipe
+
 // One warp per pair: lane k sums term k over the pair's items in order.
 __global__ void reduce_kernel(const double* __restrict__ partials, const int2* __restrict__ span,
                               int32_t n_items_single, int64_t n_pairs,
@@ -758,7 +965,8 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  return device_sm_count() * ((neighbours == 27 || variant == 1) ? 2 : VGICP_MIN_BLOCKS);
+  return device_sm_count() *
+         ((neighbours == 27 || variant == 1 || variant == 3) ? 2 : VGICP_MIN_BLOCKS);
 }
 
 int launch_linearize(const LinLaunch& L, cudaStream_t st) {
@@ -771,6 +979,8 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     linearize_simple_kernel<27><<<grid, kSimpleThreads, 0, st>>>(L);
   } else if (variant == 1) {
     linearize_simple_kernel<1><<<grid, kSimpleThreads, 0, st>>>(L);
+  } else if (variant == 3) {
+    pipe::linearize_pipe_kernel<<<grid, pipe::kThreads, 0, st>>>(L);
   } else {
     static bool attr_set[64] = {false};
     int dev = 0;

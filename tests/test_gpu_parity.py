@@ -267,7 +267,7 @@ def test_pose_validation(dev):
         api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 1]], T[None])
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_kernel_variants_match_oracle(dev, variant):
     tp, tc, sp, sc, T, r = cases.room()
     vm = api.VoxelMap.build(cu(tp), cu(tc), r)
@@ -280,7 +280,7 @@ def test_kernel_variants_match_oracle(dev, variant):
     check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}")
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_map_as_source(dev, variant):
     """A map's own (voxel-grouped) cloud as the source gives the same factor as the
     original cloud, within tolerance, and matches the oracle."""
@@ -302,3 +302,34 @@ def test_map_as_source(dev, variant):
         sp, sc = w.clouds.cloud(i)
         ref = oracle.linearize(omaps[j], sp, sc, w.poses[p], nthreads=0)
         check_factor(b.out[p], b.inliers[p], ref, f"pair {p}")
+
+
+def test_plan_graph_autotune_matches_oracle_and_batched(dev):
+    """The plan (work list built once, autotuned launch shape, CUDA graph replay)
+    gives the oracle's factors; replays with the same poses are bitwise identical
+    and a replay with other poses equals a fresh batched call of that shape."""
+    w = cases.workload_with_knn_covs("outdoor", seed=33, n_submaps=10, neighbours=3)
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    plan = api.Plan(maps, maps, w.pairs)
+    info = plan.autotune(w.poses)
+    assert info["variant"] in (1, 2, 3) and info["item_points"] in (4096, 8192, 16384, 32768)
+    a = plan.execute(w.poses).out.clone()
+    b = plan.execute(w.poses).out.clone()
+    assert torch.equal(a, b)
+    poses2 = np.stack([synth.perturb_pose(np.random.default_rng(k), T, 0.02, 0.5)
+                       for k, T in enumerate(w.poses)])
+    c = plan.execute(poses2)
+    d = api.linearize_batched(maps, maps, w.pairs, poses2, tile=info["item_points"],
+                              variant=info["variant"])
+    assert torch.equal(c.out, d.out) and torch.equal(c.inliers, d.inliers)
+    omaps = {}
+    for p, (j, i) in enumerate(w.pairs[:6]):
+        if j not in omaps:
+            tp, tc = w.clouds.cloud(j)
+            omaps[j] = oracle.build_voxelmap(tp, tc, w.resolution)
+        sp, sc = w.clouds.cloud(i)
+        ref = oracle.linearize(omaps[j], sp, sc, poses2[p], nthreads=0)
+        check_factor(c.out[p], c.inliers[p], ref, f"plan pair {p}")
+    plan.close()
