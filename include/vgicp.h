@@ -199,6 +199,35 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
                             const double* poses, double* out, int64_t* inliers,
                             const vgicp_lin_opts* opts, vgicp_stream_t stream);
 
+/* Cost and gradient of n_pairs factors (same arguments as
+ * vgicp_linearize_batched), for differentiable use of Eq. 2 with respect to
+ * the right perturbation xi = [omega; v] of each pose:
+ *   mode 1: err only;
+ *   mode 2: gradient 2 J^T W d with W held at the pose (= 2 b, the
+ *           Gauss-Newton gradient) and err;
+ *   mode 3: the exact gradient, which adds for each omega_i the change of
+ *           W = (C' + R C R^T)^-1 with the rotation, -u^T (dM/domega_i) u with
+ *           u = W d, and err.
+ * out: device n_pairs x 7 doubles (gradient 6, err 1); inliers as before.
+ * Runs the one-point-per-thread kernel. */
+int vgicp_evaluate_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                           int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                           const double* poses, int32_t mode, double* out, int64_t* inliers,
+                           const vgicp_lin_opts* opts, vgicp_stream_t stream);
+
+/* Host binary64 pose algebra for optimizers (no device work; never fails on
+ * finite input except solve6 on a non positive definite system).
+ *   vgicp_se3_exp: T (row-major 4x4) = Exp(xi), xi = [omega; v].
+ *   vgicp_se3_right_jacobian: J (row-major 6x6) with
+ *     Exp(xi + d) = Exp(xi) Exp(J d) + O(|d|^2).
+ *   vgicp_pose_mul: C = A B (4x4, C may alias A or B).
+ *   vgicp_solve6: xi = -(H + lambda diag(H))^-1 b by Cholesky (lambda >= 0;
+ *     0 gives the Gauss-Newton step of err ~ err + 2 b^T xi + xi^T H xi). */
+int vgicp_se3_exp(const double* xi, double* T);
+int vgicp_se3_right_jacobian(const double* xi, double* J);
+int vgicp_pose_mul(const double* A, const double* B, double* C);
+int vgicp_solve6(const double* H, const double* b, double lambda, double* xi);
+
 /* ------------------------------------------------------------------------ */
 /* Plans: a fixed factor set linearized at every optimizer iteration          */
 /* (Sec. III-A re-linearizes each factor per iteration; Sec. III-F links every */

@@ -300,3 +300,92 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# host binary64 pose algebra (library calls)
+# ---------------------------------------------------------------------------
+
+def se3_exp(xi) -> np.ndarray:
+    """Exp(xi) for xi = [omega; v] (4x4, binary64)."""
+    x = np.ascontiguousarray(np.asarray(xi, dtype=np.float64).reshape(6))
+    T = np.empty((4, 4))
+    check(_lib.load().vgicp_se3_exp(x.ctypes.data_as(ctypes.c_void_p),
+                                    T.ctypes.data_as(ctypes.c_void_p)))
+    return T
+
+
+def se3_right_jacobian(xi) -> np.ndarray:
+    """J with Exp(xi + d) = Exp(xi) Exp(J d) + O(|d|^2) (6x6)."""
+    x = np.ascontiguousarray(np.asarray(xi, dtype=np.float64).reshape(6))
+    J = np.empty((6, 6))
+    check(_lib.load().vgicp_se3_right_jacobian(x.ctypes.data_as(ctypes.c_void_p),
+                                               J.ctypes.data_as(ctypes.c_void_p)))
+    return J
+
+
+def pose_mul(A, B) -> np.ndarray:
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(4, 4))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(4, 4))
+    C = np.empty((4, 4))
+    check(_lib.load().vgicp_pose_mul(A.ctypes.data_as(ctypes.c_void_p),
+                                     B.ctypes.data_as(ctypes.c_void_p),
+                                     C.ctypes.data_as(ctypes.c_void_p)))
+    return C
+
+
+def solve6(H, b, damping: float = 0.0) -> np.ndarray:
+    """-(H + damping diag(H))^-1 b by Cholesky (binary64)."""
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(6, 6))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(6))
+    x = np.empty(6)
+    check(_lib.load().vgicp_solve6(H.ctypes.data_as(ctypes.c_void_p),
+                                   b.ctypes.data_as(ctypes.c_void_p), float(damping),
+                                   x.ctypes.data_as(ctypes.c_void_p)))
+    return x
+
+
+COST, GRADIENT, EXACT_GRADIENT = 1, 2, 3
+
+
+def evaluate_batched(maps, sources, pairs, poses, mode=GRADIENT, neighbours=1, tile=0,
+                     stream=None):
+    """Cost (mode 1), Gauss-Newton gradient 2 J^T W d (mode 2) or exact gradient
+    (mode 3) of each factor.  Returns (grad (P, 6), err (P,), inliers (P,)), device."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0]
+    poses = _pose_array(poses, P)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((P, 7), dtype=torch.float64, device=dev)
+    inl = torch.empty(P, dtype=torch.int64, device=dev)
+    clouds = make_clouds(sources)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    opts = LinOpts(int(neighbours), int(tile), 0, 0, None, None, None, None)
+    check(_lib.load().vgicp_evaluate_batched(arr, len(maps), clouds, len(sources),
+                                             pairs.ctypes.data_as(ctypes.c_void_p), P,
+                                             poses.ctypes.data_as(ctypes.c_void_p), int(mode),
+                                             ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(inl.data_ptr()), ctypes.byref(opts),
+                                             _stream_ptr(stream)))
+    return out[:, :6], out[:, 6], inl
+
+
+def gauss_newton(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T0, max_iters=30,
+                 tol=1e-9, damping=0.0, neighbours=1):
+    """Minimise one factor's cost over T = T_target_source: linearize on the GPU
+    (H, b, err at T), solve the 6x6 system on the host in binary64 (Cholesky),
+    update T <- T Exp(xi) in binary64.  Returns (T, history) with history the
+    list of (err, |xi|) per iteration."""
+    T = np.ascontiguousarray(np.asarray(T0, dtype=np.float64).reshape(4, 4)).copy()
+    hist = []
+    out = torch.empty(RESULT_SIZE, dtype=torch.float64, device=points.device)
+    inl = torch.empty((), dtype=torch.int64, device=points.device)
+    for _ in range(max_iters):
+        linearize(vmap, points, covs, T, neighbours=neighbours, out=out, inliers=inl)
+        o = out.cpu().numpy()
+        xi = solve6(o[:36], o[36:42], damping)
+        T = pose_mul(T, se3_exp(xi))
+        hist.append((float(o[42]), float(np.linalg.norm(xi))))
+        if np.linalg.norm(xi) < tol:
+            break
+    return T, hist

@@ -469,10 +469,33 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   return rc;
 }
 
+static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                        int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                        const double* poses, double* out, int64_t* inliers,
+                        const vgicp_lin_opts* opts, vgicp_stream_t stream, int32_t mode);
+
 int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
                             int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                             const double* poses, double* out, int64_t* inliers,
                             const vgicp_lin_opts* opts, vgicp_stream_t stream) {
+  return batched_impl(maps, n_maps, sources, n_sources, pairs, n_pairs, poses, out, inliers, opts,
+                      stream, 0);
+}
+
+int vgicp_evaluate_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                           int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                           const double* poses, int32_t mode, double* out, int64_t* inliers,
+                           const vgicp_lin_opts* opts, vgicp_stream_t stream) {
+  if (mode < 1 || mode > 3)
+    return set_error(VGICP_ERR_INVALID_ARG, "mode must be 1 (cost), 2 (gradient) or 3 (exact)");
+  return batched_impl(maps, n_maps, sources, n_sources, pairs, n_pairs, poses, out, inliers, opts,
+                      stream, mode);
+}
+
+static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                        int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                        const double* poses, double* out, int64_t* inliers,
+                        const vgicp_lin_opts* opts, vgicp_stream_t stream, int32_t mode) {
   g_error.clear();
   if (n_pairs < 0) return set_error(VGICP_ERR_INVALID_ARG, "negative n_pairs");
   if (n_pairs == 0) return VGICP_OK;
@@ -585,6 +608,7 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
     L.partials = reinterpret_cast<double*>(dev + o_part);
     L.status = reinterpret_cast<int32_t*>(dev + o_status);
     L.neighbours = neighbours;
+    L.mode = mode;
     L.variant = opts ? opts->variant : 0;
     L.grid = opts ? opts->grid : 0;
     L.ev_start = opts ? static_cast<cudaEvent_t>(opts->kernel_start) : nullptr;
@@ -592,7 +616,7 @@ int vgicp_linearize_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_
     rc = launch_linearize(L, st);
     if (rc == VGICP_OK)
       rc = launch_reduce(L.partials, reinterpret_cast<const int2*>(dev + o_span), 0, n_pairs,
-                         L.status, out, inliers, st);
+                         L.status, out, inliers, st, mode);
   }
   e = cudaFreeAsync(dev, st);
   if (rc == VGICP_OK && e != cudaSuccess) rc = check_cuda(e, "cudaFreeAsync");

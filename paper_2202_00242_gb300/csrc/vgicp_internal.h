@@ -104,6 +104,7 @@ struct LinLaunch {
   int32_t* corr_out;
   int32_t* qkey_out;
   int32_t neighbours;
+  int32_t mode;              // 0 linearize (H, b, err); 1 err; 2 gradient; 3 exact gradient
   int32_t variant;           // 1-neighbour kernel: 1 per-point, 2 staged (0 = default)
   int32_t grid;              // 0 = automatic
   cudaEvent_t ev_start;      // optional, recorded around the kernel
@@ -121,7 +122,7 @@ int default_variant();
 // n_items_single items.  A nonzero *status turns every output into NaN.
 int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
                   int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
-                  cudaStream_t st);
+                  cudaStream_t st, int32_t mode = 0);
 
 int device_sm_count();
 

@@ -627,7 +627,78 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
 // One point per thread (1 or 27 neighbours); the lookups and records come from
 // global memory through L1.
 // ---------------------------------------------------------------------------
-template <int NEIGH>
+// Cost and gradient of one term, for the differentiable interface:
+//   MODE 1: err only;  MODE 2: + g = 2 J^T W d (W held, the Gauss-Newton gradient);
+//   MODE 3: + the change of W with the rotation: for omega_i the exact derivative
+//           adds -u^T dM/domega_i u = 2 (u' x C_k u')_i, u' = W' d' (source frame).
+// Accumulators: 0..5 gradient, 6 err, 28 inlier count.
+template <int MODE>
+__device__ __forceinline__ void eval_term(float* acc, const Pose32& P, float x, float y, float z,
+                                          const float* c, float qx, float qy, float qz,
+                                          const float4 r0, const float4 r1, const float4 r2) {
+  const float* R = P.R;
+  const float tx = r0.x - qx, ty = r0.y - qy, tz = r0.z - qz;
+  const float d0 = fmaf(R[0], tx, fmaf(R[3], ty, R[6] * tz));
+  const float d1 = fmaf(R[1], tx, fmaf(R[4], ty, R[7] * tz));
+  const float d2 = fmaf(R[2], tx, fmaf(R[5], ty, R[8] * tz));
+  const float v00 = r1.x, v01 = r1.y, v02 = r1.z, v11 = r1.w, v12 = r2.x, v22 = r2.y;
+  const float a00 = fmaf(v00, R[0], fmaf(v01, R[3], v02 * R[6]));
+  const float a01 = fmaf(v00, R[1], fmaf(v01, R[4], v02 * R[7]));
+  const float a02 = fmaf(v00, R[2], fmaf(v01, R[5], v02 * R[8]));
+  const float a10 = fmaf(v01, R[0], fmaf(v11, R[3], v12 * R[6]));
+  const float a11 = fmaf(v01, R[1], fmaf(v11, R[4], v12 * R[7]));
+  const float a12 = fmaf(v01, R[2], fmaf(v11, R[5], v12 * R[8]));
+  const float a20 = fmaf(v02, R[0], fmaf(v12, R[3], v22 * R[6]));
+  const float a21 = fmaf(v02, R[1], fmaf(v12, R[4], v22 * R[7]));
+  const float a22 = fmaf(v02, R[2], fmaf(v12, R[5], v22 * R[8]));
+  const float m00 = fmaf(R[0], a00, fmaf(R[3], a10, fmaf(R[6], a20, c[0])));
+  const float m01 = fmaf(R[0], a01, fmaf(R[3], a11, fmaf(R[6], a21, c[1])));
+  const float m02 = fmaf(R[0], a02, fmaf(R[3], a12, fmaf(R[6], a22, c[2])));
+  const float m11 = fmaf(R[1], a01, fmaf(R[4], a11, fmaf(R[7], a21, c[3])));
+  const float m12 = fmaf(R[1], a02, fmaf(R[4], a12, fmaf(R[7], a22, c[4])));
+  const float m22 = fmaf(R[2], a02, fmaf(R[5], a12, fmaf(R[8], a22, c[5])));
+  const float i00 = fmaf(m11, m22, -m12 * m12);
+  const float i01 = fmaf(m02, m12, -m01 * m22);
+  const float i02 = fmaf(m01, m12, -m02 * m11);
+  const float i11 = fmaf(m00, m22, -m02 * m02);
+  const float i12 = fmaf(m01, m02, -m00 * m12);
+  const float i22 = fmaf(m00, m11, -m01 * m01);
+  const float det = fmaf(m00, i00, fmaf(m01, i01, m02 * i02));
+  const float sc = __frcp_rn(det);
+  const float u0 = fmaf(i00, d0, fmaf(i01, d1, i02 * d2)) * sc;
+  const float u1 = fmaf(i01, d0, fmaf(i11, d1, i12 * d2)) * sc;
+  const float u2 = fmaf(i02, d0, fmaf(i12, d1, i22 * d2)) * sc;
+  acc[6] = fmaf(d0, u0, fmaf(d1, u1, fmaf(d2, u2, acc[6])));
+  if (MODE >= 2) {
+    acc[0] = fmaf(2.0f * u1, z, fmaf(-2.0f * u2, y, acc[0]));
+    acc[1] = fmaf(2.0f * u2, x, fmaf(-2.0f * u0, z, acc[1]));
+    acc[2] = fmaf(2.0f * u0, y, fmaf(-2.0f * u1, x, acc[2]));
+    acc[3] -= 2.0f * u0;
+    acc[4] -= 2.0f * u1;
+    acc[5] -= 2.0f * u2;
+  }
+  if (MODE == 3) {
+    const float k0 = fmaf(c[0], u0, fmaf(c[1], u1, c[2] * u2));
+    const float k1 = fmaf(c[1], u0, fmaf(c[3], u1, c[4] * u2));
+    const float k2 = fmaf(c[2], u0, fmaf(c[4], u1, c[5] * u2));
+    acc[0] = fmaf(2.0f * u1, k2, fmaf(-2.0f * u2, k1, acc[0]));
+    acc[1] = fmaf(2.0f * u2, k0, fmaf(-2.0f * u0, k2, acc[1]));
+    acc[2] = fmaf(2.0f * u0, k1, fmaf(-2.0f * u1, k0, acc[2]));
+  }
+  acc[28] += 1.0f;
+}
+
+template <int MODE>
+__device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float y, float z,
+                                     const float* c, float qx, float qy, float qz,
+                                     const float4 r0, const float4 r1, const float4 r2) {
+  if (MODE == 0)
+    add_term(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
+  else
+    eval_term<MODE>(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
+}
+
+template <int NEIGH, int MODE>
 __global__ void __launch_bounds__(kSimpleThreads, 2)
     linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kSimpleThreads / 32][kAcc];
@@ -675,7 +746,7 @@ __global__ void __launch_bounds__(kSimpleThreads, 2)
         float4 a0, a1, a2;
         const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
         if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-        if (vid >= 0) add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+        if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
         continue;
       }
       if (L.corr_out) {
@@ -689,7 +760,7 @@ __global__ void __launch_bounds__(kSimpleThreads, 2)
             float4 a0, a1, a2;
             const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
             if (vid < 0) continue;
-            add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+            term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
           }
     }
 
@@ -925,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __gri
 __global__ void reduce_kernel(const double* __restrict__ partials, const int2* __restrict__ span,
                               int32_t n_items_single, int64_t n_pairs,
                               const int32_t* __restrict__ status, double* __restrict__ out,
-                              int64_t* __restrict__ inliers) {
+                              int64_t* __restrict__ inliers, int32_t mode) {
   const int64_t pair = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
@@ -935,6 +1006,11 @@ __global__ void reduce_kernel(const double* __restrict__ partials, const int2* _
   if (lane < kAcc)
     for (int32_t it = a; it < b; ++it) s += partials[(int64_t)it * kPartialStride + lane];
   if (status && *status != 0) s = __longlong_as_double(0x7FF8000000000000ll);  // NaN
+  if (mode != 0) {  // gradient (6) and err (1)
+    if (lane < 7) out[pair * 7 + lane] = s;
+    if (lane == 28) inliers[pair] = (status && *status != 0) ? -1 : (int64_t)llrint(s);
+    return;
+  }
   double* o = out + pair * 43;
   constexpr int ww_r[6] = {0, 0, 0, 1, 1, 2}, ww_c[6] = {0, 1, 2, 1, 2, 2};
   if (lane < 6) {
@@ -971,14 +1047,25 @@ int linearize_grid(int neighbours, int variant) {
 
 int launch_linearize(const LinLaunch& L, cudaStream_t st) {
   if (L.n_items <= 0) return VGICP_OK;
-  const int variant = L.variant ? L.variant : default_variant();
+  const int variant = L.mode != 0 ? 1 : (L.variant ? L.variant : default_variant());
   int grid = L.grid > 0 ? L.grid : linearize_grid(L.neighbours, variant);
   grid = std::min(grid, L.n_items);
   if (L.ev_start) VGICP_CUDA_TRY(cudaEventRecord(L.ev_start, st));
-  if (L.neighbours == 27) {
-    linearize_simple_kernel<27><<<grid, kSimpleThreads, 0, st>>>(L);
+  if (L.mode != 0) {
+    // cost / gradient evaluations use the per-point kernel
+    if (L.neighbours == 27) {
+      if (L.mode == 1) linearize_simple_kernel<27, 1><<<grid, kSimpleThreads, 0, st>>>(L);
+      else if (L.mode == 2) linearize_simple_kernel<27, 2><<<grid, kSimpleThreads, 0, st>>>(L);
+      else linearize_simple_kernel<27, 3><<<grid, kSimpleThreads, 0, st>>>(L);
+    } else {
+      if (L.mode == 1) linearize_simple_kernel<1, 1><<<grid, kSimpleThreads, 0, st>>>(L);
+      else if (L.mode == 2) linearize_simple_kernel<1, 2><<<grid, kSimpleThreads, 0, st>>>(L);
+      else linearize_simple_kernel<1, 3><<<grid, kSimpleThreads, 0, st>>>(L);
+    }
+  } else if (L.neighbours == 27) {
+    linearize_simple_kernel<27, 0><<<grid, kSimpleThreads, 0, st>>>(L);
   } else if (variant == 1) {
-    linearize_simple_kernel<1><<<grid, kSimpleThreads, 0, st>>>(L);
+    linearize_simple_kernel<1, 0><<<grid, kSimpleThreads, 0, st>>>(L);
   } else if (variant == 3) {
     pipe::linearize_pipe_kernel<<<grid, pipe::kThreads, 0, st>>>(L);
   } else {
@@ -1001,12 +1088,12 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
 
 int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
                   int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
-                  cudaStream_t st) {
+                  cudaStream_t st, int32_t mode) {
   if (n_pairs <= 0) return VGICP_OK;
   const int warps = 8;
   const int64_t blocks = (n_pairs + warps - 1) / warps;
   reduce_kernel<<<(unsigned)blocks, warps * 32, 0, st>>>(partials, span, n_items_single, n_pairs,
-                                                         status, out, inliers);
+                                                         status, out, inliers, mode);
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return VGICP_OK;

@@ -349,7 +349,7 @@ def outdoor_submaps(seed=3, n_submaps=500, n_min=30000, n_max=80000, neighbours=
     there are n_submaps * neighbours pairs.  ``poses`` are the true relative poses
     perturbed by ``perturb`` = (sigma_t [m], sigma_rot [deg])."""
     rng = np.random.default_rng(seed)
-    lap_len = n_submaps * spacing / laps
+    lap_len = max(n_submaps * spacing / laps, 150.0)
     x, y, hd = _loop_path(n_submaps, lap_len, laps, lateral=3.0)
     # buildings along the first lap's path, both sides
     segs, zs = [], []
@@ -369,7 +369,8 @@ def outdoor_submaps(seed=3, n_submaps=500, n_min=30000, n_max=80000, neighbours=
                 p0, p1 = corners[k], corners[(k + 1) % 4]
                 segs.append([p0[0], p0[1], p1[0], p1[1]])
                 zs.append([0.0, h])
-    walls = Walls(np.array(segs), np.array(zs))
+    walls = Walls(np.array(segs, dtype=np.float64).reshape(-1, 4),
+                  np.array(zs, dtype=np.float64).reshape(-1, 2))
     if size_dist == "loguniform":
         sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_submaps)).astype(np.int64)
     else:
