@@ -229,6 +229,25 @@ int vgicp_pose_mul(const double* A, const double* B, double* C);
 int vgicp_solve6(const double* H, const double* b, double lambda, double* xi);
 
 /* ------------------------------------------------------------------------ */
+/* Admission: factor sets larger than device memory (host-only planning).      */
+/* ------------------------------------------------------------------------ */
+
+/* Device bytes a voxel map of n_points occupies (all its buffers), for budgets. */
+int64_t vgicp_voxelmap_bytes(int64_t n_points, const vgicp_map_opts* opts);
+
+/* Assigns every pair to a batch whose working set (its target maps and source
+ * clouds, counted once each) fits in budget bytes.  Greedy over the pairs in
+ * (target, source) order, which keeps the pairs of one target together.
+ * map_bytes: host n_maps; src_bytes: host n_sources, or ignored when
+ * src_is_map != 0 (each source is the map of the same index, counted once).
+ * batch_of_pair: host n_pairs output; *n_batches: output.  A pair whose own
+ * working set exceeds the budget is an error. */
+int vgicp_admission_schedule(const int64_t* map_bytes, int32_t n_maps, const int64_t* src_bytes,
+                             int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                             int64_t budget, int32_t src_is_map, int32_t* batch_of_pair,
+                             int32_t* n_batches);
+
+/* ------------------------------------------------------------------------ */
 /* Plans: a fixed factor set linearized at every optimizer iteration          */
 /* (Sec. III-A re-linearizes each factor per iteration; Sec. III-F links every */
 /* overlapping submap pair).  The work list is built once, the launch shape   */

@@ -389,3 +389,69 @@ def gauss_newton(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T0, m
         if np.linalg.norm(xi) < tol:
             break
     return T, hist
+
+
+# ---------------------------------------------------------------------------
+# admission: factor sets whose maps and clouds exceed device memory
+# ---------------------------------------------------------------------------
+
+def voxelmap_bytes(n_points: int, max_probe=0, capacity_factor=0) -> int:
+    opts = _map_opts(max_probe, capacity_factor)
+    return int(_lib.load().vgicp_voxelmap_bytes(int(n_points), ctypes.byref(opts)))
+
+
+def admission_schedule(map_bytes, pairs, budget, src_bytes=None):
+    """Batch index of every pair so that each batch's maps and sources fit in
+    ``budget`` bytes (sources are the maps themselves when src_bytes is None)."""
+    mb = np.ascontiguousarray(np.asarray(map_bytes, dtype=np.int64))
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    sb = None if src_bytes is None else np.ascontiguousarray(np.asarray(src_bytes, np.int64))
+    out = np.empty(pairs.shape[0], dtype=np.int32)
+    nb = ctypes.c_int32()
+    check(_lib.load().vgicp_admission_schedule(
+        mb.ctypes.data_as(ctypes.c_void_p), mb.shape[0],
+        None if sb is None else sb.ctypes.data_as(ctypes.c_void_p),
+        0 if sb is None else sb.shape[0], pairs.ctypes.data_as(ctypes.c_void_p), pairs.shape[0],
+        int(budget), 1 if sb is None else 0, out.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(nb)))
+    return out, nb.value
+
+
+def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution, budget,
+                       neighbours=27, tile=0, stream=None):
+    """Linearize factors among submaps that live in host memory, batch by batch:
+    each batch's submaps are uploaded, built into voxel maps (which also serve
+    as the sources), linearized in one batched launch, and released.  Returns
+    (out (P, 43) float64 host, inliers (P,) host, n_batches)."""
+    off = np.asarray(offsets, dtype=np.int64)
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0]
+    sizes = np.diff(off)
+    mbytes = np.array([voxelmap_bytes(n) + 36 * n for n in sizes], dtype=np.int64)
+    batch, nb = admission_schedule(mbytes, pairs, budget)
+    out = np.zeros((P, RESULT_SIZE))
+    inl = np.zeros(P, dtype=np.int64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for b in range(nb):
+        sel = np.nonzero(batch == b)[0]
+        used = np.unique(pairs[sel].ravel())
+        local = {int(m): k for k, m in enumerate(used)}
+        boff = np.concatenate([[0], np.cumsum(sizes[used])]).astype(np.int64)
+        pts = torch.empty((int(boff[-1]), 3), dtype=torch.float32, device=dev)
+        cvs = torch.empty((int(boff[-1]), 6), dtype=torch.float32, device=dev)
+        for k, m in enumerate(used):
+            pts[boff[k]:boff[k + 1]].copy_(torch.from_numpy(points_host[off[m]:off[m + 1]]),
+                                           non_blocking=True)
+            cvs[boff[k]:boff[k + 1]].copy_(torch.from_numpy(covs_host[off[m]:off[m + 1]]),
+                                           non_blocking=True)
+        maps = build_voxelmaps(pts, cvs, boff, resolution, stream=stream)
+        maps[0].status()
+        lp = np.array([[local[int(j)], local[int(i)]] for j, i in pairs[sel]], dtype=np.int32)
+        res = linearize_batched(maps, maps, lp, poses[sel], neighbours=neighbours, tile=tile,
+                                stream=stream)
+        out[sel] = res.out.cpu().numpy()
+        inl[sel] = res.inliers.cpu().numpy()
+        for m in maps:
+            m.close()
+        del pts, cvs
+    return out, inl, nb

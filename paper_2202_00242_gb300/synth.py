@@ -79,16 +79,18 @@ def to_frame(points, normals, T_world_frame):
 
 def surface_covariances(normals, eps=1e-3):
     """(n, 6) float32 upper triangles of I - (1 - eps) n n^T."""
-    n = np.asarray(normals, dtype=np.float64)
     s = 1.0 - eps
-    out = np.empty((n.shape[0], 6), dtype=np.float64)
-    out[:, 0] = 1.0 - s * n[:, 0] * n[:, 0]
-    out[:, 1] = -s * n[:, 0] * n[:, 1]
-    out[:, 2] = -s * n[:, 0] * n[:, 2]
-    out[:, 3] = 1.0 - s * n[:, 1] * n[:, 1]
-    out[:, 4] = -s * n[:, 1] * n[:, 2]
-    out[:, 5] = 1.0 - s * n[:, 2] * n[:, 2]
-    return out.astype(np.float32)
+    out = np.empty((len(normals), 6), dtype=np.float32)
+    for a in range(0, len(normals), 1 << 22):  # bounded float64 temporaries
+        n = np.asarray(normals[a:a + (1 << 22)], dtype=np.float64)
+        o = out[a:a + (1 << 22)]
+        o[:, 0] = 1.0 - s * n[:, 0] * n[:, 0]
+        o[:, 1] = -s * n[:, 0] * n[:, 1]
+        o[:, 2] = -s * n[:, 0] * n[:, 2]
+        o[:, 3] = 1.0 - s * n[:, 1] * n[:, 1]
+        o[:, 4] = -s * n[:, 1] * n[:, 2]
+        o[:, 5] = 1.0 - s * n[:, 2] * n[:, 2]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -384,8 +386,8 @@ def outdoor_submaps(seed=3, n_submaps=500, n_min=30000, n_max=80000, neighbours=
         world.append(Tw)
         p, q = sample_scan(rng, walls, np.array([x[i], y[i], 1.8]), int(sizes[i]), radius, sigma)
         pl, ql = to_frame(p, q, Tw)
-        pts.append(pl)
-        nrm.append(ql)
+        pts.append(pl.astype(np.float32))  # the packed clouds are float32 anyway
+        nrm.append(ql.astype(np.float32))
     clouds = _pack(pts, nrm)
     centers = np.column_stack([x, y])
     pairs = []
