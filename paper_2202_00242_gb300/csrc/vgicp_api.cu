@@ -459,7 +459,7 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), part_bytes + 256, st));
   L.partials = reinterpret_cast<double*>(scratch);
   L.status = reinterpret_cast<int32_t*>(scratch + part_bytes);
-  cudaError_t e = cudaMemsetAsync(L.status, 0, sizeof(int32_t), st);
+  cudaError_t e = cudaMemsetAsync(L.status, 0, 2 * sizeof(int32_t), st);
   rc = e == cudaSuccess ? VGICP_OK : check_cuda(e, "cudaMemsetAsync");
   if (rc == VGICP_OK) rc = launch_linearize(L, st);
   if (rc == VGICP_OK)
@@ -507,8 +507,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2, 3 or 4");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -593,7 +593,7 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
   cudaError_t e = cudaMemcpyAsync(dev, host.data(), upload, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) rc = check_cuda(e, "cudaMemcpyAsync(plan)");
   if (rc == VGICP_OK) {
-    e = cudaMemsetAsync(dev + o_status, 0, sizeof(int32_t), st);
+    e = cudaMemsetAsync(dev + o_status, 0, 2 * sizeof(int32_t), st);
     if (e != cudaSuccess) rc = check_cuda(e, "cudaMemsetAsync");
   }
   if (rc == VGICP_OK) {
@@ -682,8 +682,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2, 3 or 4");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =
@@ -724,7 +724,7 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   L.status = reinterpret_cast<int32_t*>(scratch + (size_t)kNoAllocMaxItems * kPartialStride);
   // the array keeps the previous call's contents: the status word must start at
   // zero; every partial the reduction reads is written by this call
-  VGICP_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(int32_t), st));
+  VGICP_CUDA_TRY(cudaMemsetAsync(L.status, 0, 2 * sizeof(int32_t), st));
   rc = launch_linearize(L, st);
   if (rc == VGICP_OK)
     rc = launch_reduce(L.partials, nullptr, (int32_t)n_items, 1, L.status, out, inliers, st);

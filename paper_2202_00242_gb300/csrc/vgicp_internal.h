@@ -100,7 +100,9 @@ struct LinLaunch {
   MapDesc single_map;
   SrcDesc single_src;
   double* partials;          // n_items x kPartialStride
-  int32_t* status;           // device int: nonzero after an internal wait timeout
+  int32_t* status;           // device int[2]: [0] nonzero after an internal wait timeout;
+                             // [1] work-item counter of the dynamically scheduled kernels
+                             //     (both zeroed before every launch)
   int32_t* corr_out;
   int32_t* qkey_out;
   int32_t neighbours;

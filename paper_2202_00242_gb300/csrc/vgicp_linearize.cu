@@ -698,58 +698,152 @@ __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float
     eval_term<MODE>(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
 }
 
-template <int NEIGH, int MODE>
-__global__ void __launch_bounds__(kSimpleThreads, 2)
+// ---------------------------------------------------------------------------
+// Per-point kernel: one source point per thread, dynamically scheduled work
+// items.  Occupancy is what hides the DRAM latency of the stream and the L2
+// latency of the lookup here, so the kernel keeps its registers for the 28
+// accumulators and the term arithmetic: the constants of the current work item
+// (pose, map and source descriptors) sit in shared memory and are re-read
+// (volatile) in every iteration instead of living in registers across the
+// point loop.
+// ---------------------------------------------------------------------------
+#ifndef VGICP_SIMPLE_MIN_BLOCKS
+#define VGICP_SIMPLE_MIN_BLOCKS 3
+#endif
+
+struct __align__(16) ItemConst {
+  float R[9];
+  float t[3];                 // R, t: 3 float4
+  float tmax, inv_r, margin_scale;
+  uint32_t mask;              // float4 #3
+  const VSlot* vslots;
+  const float* pts;           // #4
+  const float* covs;
+  const PairDesc* pd;         // #5
+  double r;
+  int32_t max_probe, pad;     // #6
+};
+
+__device__ __forceinline__ float4 lds_f4(const void* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ void lds_2ptr(const void* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
+               : "=l"(a), "=l"(b)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
+template <int NEIGH, int MODE, bool DBG>
+__global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
     linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kSimpleThreads / 32][kAcc];
+  __shared__ ItemConst ic;
+  __shared__ int next_item;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol = policy_evict_last_l();
 
-  for (int it = blockIdx.x; it < L.n_items; it += gridDim.x) {
+  for (int it = blockIdx.x; it < L.n_items;) {
     int pair, begin, end;
     tma::item_bounds(L, it, pair, begin, end);
-    const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-    Pose32 P;
+    if (threadIdx.x == 0) {
+      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
+      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
-    P.t[0] = pd->t[0];
-    P.t[1] = pd->t[1];
-    P.t[2] = pd->t[2];
-    P.tmax = pd->tmax;
-    const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-    const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-    const uint32_t mask = *md.vmask;
-    const uint64_t pol = policy_evict_last_l();
+      for (int k = 0; k < 9; ++k) ic.R[k] = pd->R[k];
+      ic.t[0] = pd->t[0];
+      ic.t[1] = pd->t[1];
+      ic.t[2] = pd->t[2];
+      ic.tmax = pd->tmax;
+      ic.inv_r = md.inv_r;
+      ic.margin_scale = md.margin_scale;
+      ic.mask = *md.vmask;
+      ic.vslots = md.vslots;
+      ic.pts = sd.pts;
+      ic.covs = sd.covs;
+      ic.pd = pd;
+      ic.r = md.r;
+      ic.max_probe = md.max_probe;
+    }
     uint32_t vbase = 0;
-    if (L.corr_out) vbase = *md.vbase;
+    if (DBG && L.corr_out) {
+      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+      vbase = *(L.maps ? L.maps[pd->map] : L.single_map).vbase;
+    }
+    __syncthreads();
 
     float acc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
 
-    for (int p = begin + threadIdx.x; p < end; p += blockDim.x) {
-      const float* pt = sd.pts + 3 * (int64_t)p;
+    for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float4 g3 = lds_f4(&ic.tmax);
+      uint64_t vs, ps, cs, pds;
+      lds_2ptr(&ic.vslots, vs, ps);
+      lds_2ptr(&ic.covs, cs, pds);
+      Pose32 P;
+      P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
+      P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
+      P.R[8] = g2.x;
+      P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
+      P.tmax = g3.x;
+      MapDesc md;
+      md.vslots = reinterpret_cast<const VSlot*>(vs);
+      md.inv_r = g3.y;
+      md.margin_scale = g3.z;
+      const uint32_t mask = __float_as_uint(g3.w);
+      const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+
+      const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
       const float x = __ldg(pt + 0), y = __ldg(pt + 1), z = __ldg(pt + 2);
-      const float2* cv = reinterpret_cast<const float2*>(sd.covs + 6 * (int64_t)p);
+      const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
+                                                         6 * (int64_t)p);
       const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
       const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
       const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
       const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
       int kx, ky, kz;
-      source_key(P, pd, md, x, y, z, qx, qy, qz, kx, ky, kz);
-      if (L.qkey_out) {
+      {
+        // the binary64 fallback reads r from shared memory only when taken
+        const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
+        const float m = fmaf(S, md.margin_scale, 1.1920928955078125e-7f);
+        const float yx = qx * md.inv_r, yy = qy * md.inv_r, yz = qz * md.inv_r;
+        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+        const bool ax = (rx < m) | (rx > 1.0f - m);
+        const bool ay = (ry < m) | (ry > 1.0f - m);
+        const bool az = (rz < m) | (rz > 1.0f - m);
+        kx = clamp_to_int(fx);
+        ky = clamp_to_int(fy);
+        kz = clamp_to_int(fz);
+        if (ax | ay | az) {
+          MapDesc mr;
+          mr.r = ic.r;
+          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+        }
+      }
+      if (DBG && L.qkey_out) {
         L.qkey_out[3 * (int64_t)p + 0] = kx;
         L.qkey_out[3 * (int64_t)p + 1] = ky;
         L.qkey_out[3 * (int64_t)p + 2] = kz;
       }
+      md.max_probe = ic.max_probe;
       if (NEIGH == 1) {
         float4 a0, a1, a2;
         const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-        if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+        if (DBG && L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
         if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
         continue;
       }
-      if (L.corr_out) {
+      if (DBG && L.corr_out) {
         float4 a0, a1, a2;
         const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
         L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
@@ -775,15 +869,214 @@ __global__ void __launch_bounds__(kSimpleThreads, 2)
 #pragma unroll
       for (int k = 0; k < kAcc; ++k) red[warp][k] = acc[k];
     }
+    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
+    __syncthreads();
+    if (threadIdx.x < kAcc) {
+      double s = 0.0;
+      for (int w = 0; w < kSimpleThreads / 32; ++w) s += (double)red[w][threadIdx.x];
+      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
+    }
+    it = next_item;  // read between the two barriers; rewritten only after the second
+    __syncthreads();
+  }
+}
+
+template <int NEIGH, int MODE>
+void launch_simple(const LinLaunch& L, int grid, cudaStream_t st) {
+  if (L.corr_out || L.qkey_out)
+    linearize_simple_kernel<NEIGH, MODE, true><<<grid, kSimpleThreads, 0, st>>>(L);
+  else
+    linearize_simple_kernel<NEIGH, MODE, false><<<grid, kSimpleThreads, 0, st>>>(L);
+}
+
+// ---------------------------------------------------------------------------
+// Software-pipelined per-point kernel (1 neighbour).  Each thread walks its
+// points with a stride of the block size, two points ahead on the source stream
+// and one point ahead on the lookup:
+//   point k+2: position and covariance loads in flight (registers)
+//   point k+1: key computed, first probe of its slot (two 256-bit loads) in flight
+//   point k  : probe resolved (further probes only on a collision), term added
+// so that neither the DRAM latency of the stream nor the L2 latency of the
+// lookup sits on the critical path of a point.
+// ---------------------------------------------------------------------------
+namespace pf {
+#ifndef VGICP_PF_THREADS
+#define VGICP_PF_THREADS 256
+#endif
+constexpr int kThreads = VGICP_PF_THREADS;
+#ifndef VGICP_PF_MIN_BLOCKS
+#define VGICP_PF_MIN_BLOCKS 2
+#endif
+
+struct Pt {
+  float x, y, z;
+  float2 c01, c23, c45;
+};
+__device__ __forceinline__ void load_pt(const SrcDesc& sd, int p, Pt& d) {
+  const float* pt = sd.pts + 3 * (int64_t)p;
+  d.x = __ldg(pt);
+  d.y = __ldg(pt + 1);
+  d.z = __ldg(pt + 2);
+  const float2* cv = reinterpret_cast<const float2*>(sd.covs + 6 * (int64_t)p);
+  d.c01 = __ldg(cv);
+  d.c23 = __ldg(cv + 1);
+  d.c45 = __ldg(cv + 2);
+}
+
+// First probe of a point's lookup, issued ahead of its use.
+struct Probe {
+  uint32_t a[8], b[8];
+  unsigned long long key;
+  uint32_t h;
+  bool live;  // key in range (else a miss without any load)
+};
+__device__ __forceinline__ void issue_probe(const MapDesc& md, uint32_t mask, int kx, int ky,
+                                            int kz, uint64_t pol, Probe& pr) {
+  pr.live = key_in_range(kx) && key_in_range(ky) && key_in_range(kz);
+  pr.key = pack_key(kx, ky, kz);
+  pr.h = hash_key(kx, ky, kz) & mask;
+  if (pr.live) {
+    const VSlot* t = md.vslots + pr.h;
+    ld_v8(t, pol, pr.a);
+    ld_v8(reinterpret_cast<const char*>(t) + 32, pol, pr.b);
+  }
+}
+// Resolves a probe: on a hit returns the global voxel id and fills the record.
+__device__ __forceinline__ int resolve_probe(const MapDesc& md, uint32_t mask, uint64_t pol,
+                                             Probe& pr, float4& r0, float4& r1, float4& r2) {
+  if (!pr.live) return -1;
+  uint32_t h = pr.h;
+  for (int p = 0; p < md.max_probe; ++p) {
+    if (p > 0) {
+      h = (h + 1) & mask;
+      const VSlot* t = md.vslots + h;
+      ld_v8(t, pol, pr.a);
+      ld_v8(reinterpret_cast<const char*>(t) + 32, pol, pr.b);
+    }
+    const unsigned long long k = slot_key(pr.a);
+    if (k == pr.key) {
+      r0 = make_float4(__uint_as_float(pr.a[4]), __uint_as_float(pr.a[5]),
+                       __uint_as_float(pr.a[6]), 0.f);
+      r1 = make_float4(__uint_as_float(pr.b[0]), __uint_as_float(pr.b[1]),
+                       __uint_as_float(pr.b[2]), __uint_as_float(pr.b[3]));
+      r2 = make_float4(__uint_as_float(pr.b[4]), __uint_as_float(pr.b[5]), 0.f, 0.f);
+      return (int)pr.a[2];
+    }
+    if (k == kEmptyKey) return -1;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kThreads, VGICP_PF_MIN_BLOCKS)
+    linearize_pf_kernel(const __grid_constant__ LinLaunch L) {
+  __shared__ float red[kThreads / 32][kAcc];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  __shared__ int next_item;
+  for (int it = blockIdx.x; it < L.n_items;) {
+    int pair, begin, end;
+    tma::item_bounds(L, it, pair, begin, end);
+    const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+    Pose32 P;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
+    P.t[0] = pd->t[0];
+    P.t[1] = pd->t[1];
+    P.t[2] = pd->t[2];
+    P.tmax = pd->tmax;
+    const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
+    const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
+    const uint32_t mask = *md.vmask;
+    const uint64_t pol = policy_evict_last_l();
+    uint32_t vbase = 0;
+    if (L.corr_out) vbase = *md.vbase;
+
+    float acc[kAcc];
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
+
+    const int stride = blockDim.x;
+    int p = begin + threadIdx.x;
+    Pt cur, nxt;
+    Probe pr;
+    float qx = 0.f, qy = 0.f, qz = 0.f;
+    if (p < end) {
+      load_pt(sd, p, cur);
+      qx = fmaf(P.R[0], cur.x, fmaf(P.R[1], cur.y, fmaf(P.R[2], cur.z, P.t[0])));
+      qy = fmaf(P.R[3], cur.x, fmaf(P.R[4], cur.y, fmaf(P.R[5], cur.z, P.t[1])));
+      qz = fmaf(P.R[6], cur.x, fmaf(P.R[7], cur.y, fmaf(P.R[8], cur.z, P.t[2])));
+      int kx, ky, kz;
+      source_key(P, pd, md, cur.x, cur.y, cur.z, qx, qy, qz, kx, ky, kz);
+      if (L.qkey_out) {
+        L.qkey_out[3 * (int64_t)p + 0] = kx;
+        L.qkey_out[3 * (int64_t)p + 1] = ky;
+        L.qkey_out[3 * (int64_t)p + 2] = kz;
+      }
+      issue_probe(md, mask, kx, ky, kz, pol, pr);
+    }
+    if (p + stride < end) load_pt(sd, p + stride, nxt);
+
+    for (; p < end; p += stride) {
+      // stream: point k+2
+      Pt nn;
+      const bool has_nn = p + 2 * stride < end;
+      if (has_nn) load_pt(sd, p + 2 * stride, nn);
+      // lookup: point k+1
+      Probe pn;
+      float nqx = 0.f, nqy = 0.f, nqz = 0.f;
+      const bool has_n = p + stride < end;
+      if (has_n) {
+        nqx = fmaf(P.R[0], nxt.x, fmaf(P.R[1], nxt.y, fmaf(P.R[2], nxt.z, P.t[0])));
+        nqy = fmaf(P.R[3], nxt.x, fmaf(P.R[4], nxt.y, fmaf(P.R[5], nxt.z, P.t[1])));
+        nqz = fmaf(P.R[6], nxt.x, fmaf(P.R[7], nxt.y, fmaf(P.R[8], nxt.z, P.t[2])));
+        int kx, ky, kz;
+        source_key(P, pd, md, nxt.x, nxt.y, nxt.z, nqx, nqy, nqz, kx, ky, kz);
+        if (L.qkey_out) {
+          L.qkey_out[3 * (int64_t)(p + stride) + 0] = kx;
+          L.qkey_out[3 * (int64_t)(p + stride) + 1] = ky;
+          L.qkey_out[3 * (int64_t)(p + stride) + 2] = kz;
+        }
+        issue_probe(md, mask, kx, ky, kz, pol, pn);
+      }
+      // point k
+      float4 a0, a1, a2;
+      const int vid = resolve_probe(md, mask, pol, pr, a0, a1, a2);
+      if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+      if (vid >= 0) {
+        const float c[6] = {cur.c01.x, cur.c01.y, cur.c23.x, cur.c23.y, cur.c45.x, cur.c45.y};
+        add_term(acc, P, cur.x, cur.y, cur.z, c, qx, qy, qz, a0, a1, a2);
+      }
+      cur = nxt;
+      qx = nqx;
+      qy = nqy;
+      qz = nqz;
+      pr = pn;
+      if (has_nn) nxt = nn;
+    }
+
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) {
+      float v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      acc[k] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kAcc; ++k) red[warp][k] = acc[k];
+    }
+    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
     __syncthreads();
     if (threadIdx.x < kAcc) {
       double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)red[w][threadIdx.x];
       L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
     }
+    it = next_item;  // read between the two barriers; rewritten only after the second
     __syncthreads();
   }
 }
+}  // namespace pf
 
 // ---------------------------------------------------------------------------
 // Pipelined per-warp kernel (1 neighbour).  Each warp walks 32-point chunks of
@@ -875,8 +1168,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __gri
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint64_t pol = policy_evict_last_l();
   float4* Q = queue[warp];
+  __shared__ int next_item;
 
-  for (int it = blockIdx.x; it < L.n_items; it += gridDim.x) {
+  for (int it = blockIdx.x; it < L.n_items;) {
     int pair, b, e;
     tma::item_bounds(L, it, pair, b, e);
     const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
@@ -979,6 +1273,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __gri
     tma::rs_step<2>(acc, lane);
     tma::rs_step<1>(acc, lane);
     red[warp][lane] = acc[0];
+    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
     __syncthreads();
     if (warp == 0 && lane < kAcc) {
       double t = 0.0;
@@ -986,6 +1281,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __gri
       for (int w = 0; w < kWarps; ++w) t += (double)red[w][lane];
       L.partials[(int64_t)it * kPartialStride + lane] = t;
     }
+    it = next_item;  // read between the two barriers; rewritten only after the second
     __syncthreads();
   }
 }
@@ -1041,8 +1337,9 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  return device_sm_count() *
-         ((neighbours == 27 || variant == 1 || variant == 3) ? 2 : VGICP_MIN_BLOCKS);
+  if (neighbours != 27 && variant == 4) return device_sm_count() * VGICP_PF_MIN_BLOCKS;
+  if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
+  return device_sm_count() * (variant == 3 ? 2 : VGICP_MIN_BLOCKS);
 }
 
 int launch_linearize(const LinLaunch& L, cudaStream_t st) {
@@ -1054,20 +1351,22 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
   if (L.mode != 0) {
     // cost / gradient evaluations use the per-point kernel
     if (L.neighbours == 27) {
-      if (L.mode == 1) linearize_simple_kernel<27, 1><<<grid, kSimpleThreads, 0, st>>>(L);
-      else if (L.mode == 2) linearize_simple_kernel<27, 2><<<grid, kSimpleThreads, 0, st>>>(L);
-      else linearize_simple_kernel<27, 3><<<grid, kSimpleThreads, 0, st>>>(L);
+      if (L.mode == 1) launch_simple<27, 1>(L, grid, st);
+      else if (L.mode == 2) launch_simple<27, 2>(L, grid, st);
+      else launch_simple<27, 3>(L, grid, st);
     } else {
-      if (L.mode == 1) linearize_simple_kernel<1, 1><<<grid, kSimpleThreads, 0, st>>>(L);
-      else if (L.mode == 2) linearize_simple_kernel<1, 2><<<grid, kSimpleThreads, 0, st>>>(L);
-      else linearize_simple_kernel<1, 3><<<grid, kSimpleThreads, 0, st>>>(L);
+      if (L.mode == 1) launch_simple<1, 1>(L, grid, st);
+      else if (L.mode == 2) launch_simple<1, 2>(L, grid, st);
+      else launch_simple<1, 3>(L, grid, st);
     }
   } else if (L.neighbours == 27) {
-    linearize_simple_kernel<27, 0><<<grid, kSimpleThreads, 0, st>>>(L);
+    launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
-    linearize_simple_kernel<1, 0><<<grid, kSimpleThreads, 0, st>>>(L);
+    launch_simple<1, 0>(L, grid, st);
   } else if (variant == 3) {
     pipe::linearize_pipe_kernel<<<grid, pipe::kThreads, 0, st>>>(L);
+  } else if (variant == 4) {
+    pf::linearize_pf_kernel<<<grid, pf::kThreads, 0, st>>>(L);
   } else {
     static bool attr_set[64] = {false};
     int dev = 0;
