@@ -80,13 +80,15 @@ typedef struct vgicp_map vgicp_map;
 
 typedef struct {
   int32_t max_probe;       /* linear-probe limit of the hash table; 0 = 64 */
-  int32_t capacity_factor; /* table capacity = next pow2 >= factor * n; 0 = 2 */
+  int32_t capacity_factor; /* build-table capacity = next pow2 >= factor * n; 0 = 2 */
 } vgicp_map_opts;
 
 /* Build the voxel map of one target cloud.  points: n x 3, covs: n x 6 (device,
  * read during the call's kernels only).  resolution > 0.  n >= 0 (an empty map
- * is valid).  *out receives a new handle.  Asynchronous; check
- * vgicp_voxelmap_status() before relying on the contents. */
+ * is valid).  *out receives a new handle.  The call synchronizes the stream once,
+ * after counting the voxels, to size the lookup table (capacity next pow2 >= 8 V,
+ * 64 B per slot); the rest is asynchronous: check vgicp_voxelmap_status() before
+ * relying on the contents. */
 int vgicp_build_voxelmap(const float* points, const float* covs, int64_t n, double resolution,
                          const vgicp_map_opts* opts, vgicp_stream_t stream, vgicp_map** out);
 
@@ -101,7 +103,10 @@ int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t*
 
 /* Rebuild maps in place from new clouds of the same sizes.  maps must be all
  * handles of one vgicp_build_voxelmaps() call (or the single handle of
- * vgicp_build_voxelmap()), in their original order.  No allocation. */
+ * vgicp_build_voxelmap()), in their original order.  No allocation and no
+ * synchronization: each lookup table keeps the capacity of the first build, so
+ * clouds with more voxels run at a higher load factor, and a voxel that does not
+ * fit within max_probe slots sets VGICP_ERR_HASH_FULL (build anew then). */
 int vgicp_rebuild_voxelmaps(vgicp_map* const* maps, int32_t n_maps, const float* points,
                             const float* covs, vgicp_stream_t stream);
 
@@ -135,9 +140,8 @@ typedef struct {
   int32_t grid;       /* CTAs of the persistent launch; 0 = automatic */
   int32_t variant;    /* 1-neighbour kernel: 0 = automatic, 1 = one point per thread,
                          2 = shared-memory staged (bulk asynchronous copies),
-                         3 = per-warp software pipeline with hit compaction,
-                         4 = per-point software pipeline (stream two points ahead,
-                             lookup one point ahead) */
+                         3 = per-warp hit compaction (terms evaluated in full
+                             warps from a shared-memory queue) */
   int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
                          point's own voxel (first-appearance numbering) or -1 */
   int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
@@ -234,7 +238,8 @@ int vgicp_solve6(const double* H, const double* b, double lambda, double* xi);
 /* Admission: factor sets larger than device memory (host-only planning).      */
 /* ------------------------------------------------------------------------ */
 
-/* Device bytes a voxel map of n_points occupies (all its buffers), for budgets. */
+/* Upper bound of the device bytes a voxel map of n_points occupies (all its
+ * buffers; the lookup table counted at V = n), for admission budgets. */
 int64_t vgicp_voxelmap_bytes(int64_t n_points, const vgicp_map_opts* opts);
 
 /* Assigns every pair to a batch whose working set (its target maps and source
@@ -268,7 +273,7 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
                       int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                       const vgicp_lin_opts* opts, vgicp_stream_t stream, vgicp_plan** out);
 
-/* Synchronizes.  Times each kernel variant (1-neighbour: 1, 2, 3, 4) with work items
+/* Synchronizes.  Times each kernel variant (1-neighbour: 1, 2, 3) with work items
  * of 4096, 8192, 16384 and 32768 points on these poses (host, n_pairs x 16) and
  * keeps the fastest; results then depend (within float32 rounding) on that
  * choice, and are deterministic for it. */

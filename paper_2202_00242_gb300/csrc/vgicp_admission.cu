@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "vgicp.h"
+#include "vgicp_device.cuh"
 #include "vgicp_internal.h"
 
 extern "C" {
@@ -18,7 +19,7 @@ int64_t vgicp_voxelmap_bytes(int64_t n_points, const vgicp_map_opts* opts) {
   const int64_t cf = opts && opts->capacity_factor > 0 ? opts->capacity_factor : 2;
   int64_t cap = 16, vcap = 16;
   while (cap < std::max<int64_t>(n_points, 1) * cf) cap <<= 1;
-  while (vcap < std::max<int64_t>(n_points, 8) * 2) vcap <<= 1;
+  while (vcap < std::max<int64_t>(n_points, 8) * (int64_t)vgicp::kLookupLoad) vcap <<= 1;
   // build table + lookup table + records + keys + grouped cloud + scratch
   return cap * 16 + vcap * 64 + n_points * (48 + 8 + 36 + 4 * 8) + 4096;
 }

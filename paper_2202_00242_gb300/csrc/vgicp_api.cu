@@ -116,21 +116,16 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->n_total = offsets[n_maps];
   s->slot_base.resize(n_maps);
   s->cap.resize(n_maps);
-  s->vslot_base.resize(n_maps);
-  int64_t cap_total = 0, vcap_total = 0;
+  int64_t cap_total = 0;
   for (int32_t m = 0; m < n_maps; ++m) {
     int64_t n = offsets[m + 1] - offsets[m];
     uint32_t c = next_pow2((uint64_t)std::max<int64_t>(n, 1) * (uint64_t)cf);
     s->cap[m] = c;
     s->slot_base[m] = cap_total;
     cap_total += c;
-    s->vslot_base[m] = vcap_total;
-    vcap_total += next_pow2((uint64_t)std::max<int64_t>(n, 8) * 2u);
   }
   s->cap_total = cap_total;
-  s->vcap_total = vcap_total;
-  if (s->n_total >= (int64_t)0xFFFFFFFFll || cap_total >= (int64_t)0xFFFFFFFFll ||
-      vcap_total >= (int64_t)0xFFFFFFFFll) {
+  if (s->n_total >= (int64_t)0xFFFFFFFFll || cap_total >= (int64_t)0xFFFFFFFFll) {
     delete s;
     return set_error(VGICP_ERR_INVALID_ARG, "more than 2^32-1 points or slots in one batch");
   }
@@ -145,11 +140,10 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   };
   const size_t o_point_off = take(sizeof(int64_t) * (n_maps + 1));
   const size_t o_slot_base = take(sizeof(int64_t) * n_maps);
-  const size_t o_vslot_base = take(sizeof(int64_t) * n_maps);
+  const size_t o_vslot_base = take(sizeof(int64_t) * (n_maps + 1));
   const size_t o_cap_mask = take(sizeof(uint32_t) * n_maps);
   const size_t o_vbase = take(sizeof(uint32_t) * (n_maps + 1));
   const size_t o_slots = take(sizeof(Slot) * cap_total);
-  const size_t o_vslots = take(sizeof(VSlot) * vcap_total);
   const size_t o_vmask = take(sizeof(uint32_t) * n_maps);
   const size_t o_recs = take(sizeof(float4) * kRecordF4 * n);
   const size_t o_vkeys = take(sizeof(unsigned long long) * n);
@@ -188,7 +182,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->d_cap_mask = reinterpret_cast<uint32_t*>(b + o_cap_mask);
   s->d_vbase = reinterpret_cast<uint32_t*>(b + o_vbase);
   s->d_slots = reinterpret_cast<Slot*>(b + o_slots);
-  s->d_vslots = reinterpret_cast<VSlot*>(b + o_vslots);
   s->d_vmask = reinterpret_cast<uint32_t*>(b + o_vmask);
   s->d_recs = reinterpret_cast<float4*>(b + o_recs);
   s->d_vkeys = reinterpret_cast<unsigned long long*>(b + o_vkeys);
@@ -216,16 +209,12 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
     e = cudaMemcpy(s->d_slot_base, s->slot_base.data(), sizeof(int64_t) * n_maps,
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(s->d_vslot_base, s->vslot_base.data(), sizeof(int64_t) * n_maps,
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
     e = cudaMemcpy(s->d_cap_mask, mask.data(), sizeof(uint32_t) * n_maps, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(s->d_chunks, chunks.data(), sizeof(int2) * chunks.size(),
                    cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(s->d_block);
-    delete s;
+    free_set(s);
     return check_cuda(e, "cudaMemcpy(map metadata)");
   }
   (void)st;
@@ -234,10 +223,7 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
 }
 
 void release_set(MapSet* s) {
-  if (--s->refcount == 0) {
-    cudaFree(s->d_block);
-    delete s;
-  }
+  if (--s->refcount == 0) free_set(s);
 }
 
 int sm_count_cache[64] = {0};
@@ -245,6 +231,12 @@ std::mutex sm_mutex;
 std::atomic<int64_t> g_launches{0};
 
 }  // namespace
+
+void free_set(MapSet* s) {
+  cudaFree(s->d_vblock);
+  cudaFree(s->d_block);
+  delete s;
+}
 
 int set_error(int code, const std::string& msg) {
   g_error = msg;
@@ -298,8 +290,7 @@ int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t*
   if (rc) return rc;
   rc = launch_build(s, points, covs, st);
   if (rc) {
-    cudaFree(s->d_block);
-    delete s;
+    free_set(s);
     return rc;
   }
   for (int32_t m = 0; m < n_maps; ++m) {
@@ -507,8 +498,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2, 3 or 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -682,8 +673,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2, 3 or 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =

@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "vgicp_device.cuh"
 #include "vgicp_internal.h"
@@ -354,7 +356,7 @@ __global__ void rank_counts_kernel(int64_t n_max, const uint32_t* __restrict__ n
 
 __device__ __forceinline__ uint32_t lookup_capacity(uint32_t nvox) {
   uint32_t c = 16;
-  while (c < 2u * nvox) c <<= 1;
+  while (c < kLookupLoad * nvox) c <<= 1;
   return c;
 }
 
@@ -363,10 +365,16 @@ __global__ void vslot_init_kernel(const int64_t* __restrict__ slot_base,
                                   const uint32_t* __restrict__ vbase, VSlot* vslots,
                                   uint32_t* __restrict__ vmask) {
   const int m = blockIdx.y;
-  const uint32_t cap = lookup_capacity(vbase[m + 1] - vbase[m]);
+  // the region was sized by the first build; a rebuild with more voxels runs at a
+  // higher load factor (an insertion past max_probe reports VGICP_ERR_HASH_FULL)
+  const uint32_t region = (uint32_t)(slot_base[m + 1] - slot_base[m]);
+  const uint32_t cap = min(lookup_capacity(vbase[m + 1] - vbase[m]), region);
   VSlot* t = vslots + slot_base[m];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+  {
     t[i].key = kEmptyKey;
+    t[i].spill = 0u;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) vmask[m] = cap - 1u;
 }
 
@@ -393,7 +401,8 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
     const int kz = (int)(key & fm) - kKeyBias;
     const uint32_t mask = vmask[lo];
     VSlot* t = vslots + slot_base[lo];
-    uint32_t h = hash_key(kx, ky, kz) & mask;
+    const uint32_t home = hash_key(kx, ky, kz) & mask;
+    uint32_t h = home;
     bool placed = false;
     for (int p = 0; p < max_probe; ++p) {
       if (atomicCAS(&t[h].key, kEmptyKey, key) == kEmptyKey) {
@@ -402,6 +411,7 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
       }
       h = (h + 1) & mask;
     }
+    if (placed && h != home) atomicOr(&t[home].spill, 1u);
     if (!placed) {
       set_status(status, VGICP_ERR_HASH_FULL);
       continue;
@@ -413,7 +423,6 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
     sl.mu[0] = r0.x;
     sl.mu[1] = r0.y;
     sl.mu[2] = r0.z;
-    sl.pad0 = 0.0f;
     sl.cov[0] = r1.x;
     sl.cov[1] = r1.y;
     sl.cov[2] = r1.z;
@@ -537,6 +546,41 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max, cons
   return VGICP_OK;
 }
 
+// First build of a set: reads the per-map voxel counts back (one stream
+// synchronization) and allocates each map's lookup table at capacity
+// next_pow2(max(16, kLookupLoad V)).
+int size_lookup_tables(MapSet* s, cudaStream_t st) {
+  std::vector<uint32_t> vb((size_t)s->n_maps + 1);
+  VGICP_CUDA_TRY(cudaMemcpyAsync(vb.data(), s->d_vbase, sizeof(uint32_t) * vb.size(),
+                                 cudaMemcpyDeviceToHost, st));
+  VGICP_CUDA_TRY(cudaStreamSynchronize(st));
+  s->vslot_base.assign((size_t)s->n_maps + 1, 0);
+  int64_t total = 0;
+  for (int32_t m = 0; m < s->n_maps; ++m) {
+    const uint64_t V = vb[m + 1] >= vb[m] ? vb[m + 1] - vb[m] : 0;
+    uint64_t c = 16;
+    while (c < kLookupLoad * V) c <<= 1;
+    s->vslot_base[m] = total;
+    total += (int64_t)c;
+  }
+  s->vslot_base[s->n_maps] = total;
+  if (total >= (int64_t)0xFFFFFFFFll)
+    return set_error(VGICP_ERR_INVALID_ARG, "more than 2^32-1 lookup slots in one batch");
+  cudaError_t e = cudaMalloc(&s->d_vblock, sizeof(VSlot) * (size_t)total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->d_vblock = nullptr;
+    return set_error(VGICP_ERR_OOM, "lookup table allocation of " +
+                                        std::to_string(sizeof(VSlot) * (size_t)total) +
+                                        " bytes failed");
+  }
+  s->d_vslots = static_cast<VSlot*>(s->d_vblock);
+  s->vcap_total = total;
+  VGICP_CUDA_TRY(cudaMemcpy(s->d_vslot_base, s->vslot_base.data(),
+                            sizeof(int64_t) * s->vslot_base.size(), cudaMemcpyHostToDevice));
+  return VGICP_OK;
+}
+
 int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t st) {
   const int64_t n = s->n_total;
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_status, 0, sizeof(int32_t), st));
@@ -548,6 +592,10 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   if (n == 0) {
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_num_voxels, 0, sizeof(uint32_t), st));
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vbase, 0, sizeof(uint32_t) * (s->n_maps + 1), st));
+    if (!s->d_vblock) {
+      const int rc = size_lookup_tables(s, st);
+      if (rc != VGICP_OK) return rc;
+    }
     vslot_init_kernel<<<dim3(1, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
                                                               s->d_vslots, s->d_vmask);
     VGICP_CUDA_TRY(cudaGetLastError());
@@ -569,6 +617,10 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
                                                             s->d_flag, s->d_num_voxels,
                                                             s->d_vbase);
+  if (!s->d_vblock) {
+    rc = size_lookup_tables(s, st);
+    if (rc != VGICP_OK) return rc;
+  }
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
   rc = launch_exclusive_scan(s->d_vcount, s->d_voff, n, s->d_num_voxels, s->d_scan_tmp,
                              s->d_num_valid, st);
@@ -598,8 +650,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
                                              s->d_gpts, s->d_gcovs);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
-    max_cap = std::max<int64_t>(max_cap, (m + 1 < s->n_maps ? s->vslot_base[m + 1] : s->vcap_total) -
-                                             s->vslot_base[m]);
+    max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);
   const unsigned gx = (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
   vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
                                                              s->d_vslots, s->d_vmask);

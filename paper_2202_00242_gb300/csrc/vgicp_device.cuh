@@ -35,17 +35,26 @@ constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 constexpr int kRecordF4 = 3;
 
 // Lookup table slot with the voxel Gaussian inline (64 B, 64-B aligned): one
-// probe is two independent 256-bit loads, so a lookup costs one round trip.
-//   bytes  0..31: key (u64), vid (u32), count (u32), mu' (3 x f32), pad
+// probe is two independent 256-bit loads.
+//   bytes  0..31: key (u64), vid (u32), count (u32), mu' (3 x f32), spill (u32)
 //   bytes 32..63: C' (6 x f32, xx xy xz yy yz zz), pad
-// Each map's table has capacity next_pow2(max(16, 2 V)) (decided on the device
-// after the voxels are counted) inside a region sized for the worst case V = n.
+// Linear probing from the key's home slot h.  spill (of slot h) is nonzero iff
+// some key whose home is h lies further along the probe sequence, so a lookup
+// whose home slot holds another key and has spill == 0 is a miss after one
+// round trip, like a key found at home; only the rest probe on.
+// Each map's table has capacity next_pow2(max(16, kLookupLoad V)) (decided on the
+// device after the voxels are counted) inside a region sized for the worst case
+// V = n.  The low load factor (<= 1 / kLookupLoad) keeps most keys at home.
+#ifndef VGICP_LOOKUP_LOAD
+#define VGICP_LOOKUP_LOAD 8
+#endif
+constexpr uint32_t kLookupLoad = VGICP_LOOKUP_LOAD;
 struct __align__(64) VSlot {
   unsigned long long key;
   uint32_t vid;
   uint32_t count;
   float mu[3];
-  float pad0;
+  uint32_t spill;
   float cov[6];
   float pad1[2];
 };

@@ -35,17 +35,18 @@ struct MapSet {
   std::vector<int64_t> point_off;  // n_maps + 1
   std::vector<int64_t> slot_base;  // n_maps
   std::vector<uint32_t> cap;       // n_maps
-  std::vector<int64_t> vslot_base; // n_maps: lookup-table region (worst case V = n)
-  int64_t vcap_total = 0;
+  std::vector<int64_t> vslot_base; // n_maps + 1: lookup-table regions, sized from the voxel
+  int64_t vcap_total = 0;          //   counts of the first build (empty before it)
   // device: per-map metadata
   int64_t* d_point_off = nullptr;  // n_maps + 1
   int64_t* d_slot_base = nullptr;  // n_maps
-  int64_t* d_vslot_base = nullptr; // n_maps
+  int64_t* d_vslot_base = nullptr; // n_maps + 1
   uint32_t* d_cap_mask = nullptr;  // n_maps
   uint32_t* d_vbase = nullptr;     // n_maps + 1: first global voxel index of each map
   // device: the maps
   Slot* d_slots = nullptr;                  // cap_total (build table)
-  VSlot* d_vslots = nullptr;                // vcap_total (lookup table, inline records)
+  VSlot* d_vslots = nullptr;                // vcap_total (lookup tables, inline records),
+                                            // in d_vblock
   uint32_t* d_vmask = nullptr;              // n_maps: lookup-table capacity - 1
   float4* d_recs = nullptr;                 // n_total * 3 (V <= n_total)
   unsigned long long* d_vkeys = nullptr;    // n_total (packed keys by voxel)
@@ -66,8 +67,12 @@ struct MapSet {
   uint32_t* d_num_voxels = nullptr;  // 1 (total V)
   uint32_t* d_num_valid = nullptr;   // 1 (points placed in a voxel)
   size_t scan_tmp_elems = 0;
-  void* d_block = nullptr;        // single allocation holding everything above
+  void* d_block = nullptr;        // single allocation holding everything above but d_vslots
+  void* d_vblock = nullptr;       // the lookup tables (allocated by the first build)
 };
+
+// Frees a map set's device memory and the set.
+void free_set(MapSet* s);
 
 }  // namespace vgicp
 

@@ -21,13 +21,18 @@
 // partial per work item; a second kernel sums each pair's partials in item
 // order.  The result is deterministic.
 //
-// 1-neighbour kernel (the paper's lookup): a producer warp streams tiles of
-// source points and covariances into shared memory with bulk asynchronous
-// copies (cp.async.bulk + mbarrier, 4 stages); each consumer warp looks up the
-// voxels of its 64 points, compacts the hits into a per-warp list with the
-// voxel records staged in shared memory, then evaluates the terms from shared
-// memory only, so lanes idle on misses do not cost arithmetic.
-// 27-neighbour kernel: one point per thread, the 27 lookups in a loop.
+// Work items are claimed dynamically from an atomic counter, so uneven items
+// (ragged tails of the clouds, pairs with few inliers) do not leave CTAs idle.
+//
+// Kernels (the autotuner picks among the 1-neighbour ones per factor set):
+//   1  per-point: one point per thread, item constants in shared memory so that
+//      3 CTAs of 256 threads fit per SM; the default and usually the fastest;
+//   2  staged: a producer warp streams tiles of points and covariances into
+//      shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier);
+//      consumer warps look up, compact the hits and evaluate from shared memory;
+//   3  compacting: the per-point lookup, with the hits queued per warp in shared
+//      memory and evaluated 32 at a time (no idle lanes on misses);
+//   27 neighbours: the per-point kernel with the 27 lookups in a loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,7 +142,7 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
       r2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
       return (int)a[2];
     }
-    if (k == kEmptyKey) return -1;
+    if (k == kEmptyKey || (p == 0 && a[7] == 0u)) return -1;  // empty, or nothing spilled
     h = (h + 1) & mask;
   }
   return -1;
@@ -147,12 +152,10 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
 //   0..5   H_ww (00 01 02 11 12 22)      6..14 H_wv (row-major, w rows, v cols)
 //   15..20 H_vv (00 01 02 11 12 22)      21..23 b_w   24..26 b_v   27 err
 //   28     inlier count
-__device__ __forceinline__ void add_term(float* acc, const Pose32& P, float x, float y, float z,
-                                         const float* c, float qx, float qy, float qz,
-                                         const float4 r0, const float4 r1, const float4 r2) {
-  const float* R = P.R;
-  // residual in the target frame, then rotated into the source frame
-  const float tx = r0.x - qx, ty = r0.y - qy, tz = r0.z - qz;
+__device__ __forceinline__ void add_term_t(float* acc, const float* R, float x, float y, float z,
+                                           const float* c, float tx, float ty, float tz,
+                                           const float4 r1, const float4 r2) {
+  // residual (tx, ty, tz) = mu' - q in the target frame, rotated into the source frame
   const float d0 = fmaf(R[0], tx, fmaf(R[3], ty, R[6] * tz));
   const float d1 = fmaf(R[1], tx, fmaf(R[4], ty, R[7] * tz));
   const float d2 = fmaf(R[2], tx, fmaf(R[5], ty, R[8] * tz));
@@ -216,6 +219,12 @@ __device__ __forceinline__ void add_term(float* acc, const Pose32& P, float x, f
   acc[3] = fmaf(p10, z, fmaf(-p12, x, acc[3]));
   acc[4] = fmaf(p11, x, fmaf(-p10, y, acc[4]));
   acc[5] = fmaf(p21, x, fmaf(-p20, y, acc[5]));
+}
+
+__device__ __forceinline__ void add_term(float* acc, const Pose32& P, float x, float y, float z,
+                                         const float* c, float qx, float qy, float qz,
+                                         const float4 r0, const float4 r1, const float4 r2) {
+  add_term_t(acc, P.R, x, y, z, c, r0.x - qx, r0.y - qy, r0.z - qz, r1, r2);
   acc[28] += 1.0f;
 }
 
@@ -545,7 +554,9 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       if (live[k]) {
         unsigned long long t = slot_key(sa[k]);
         uint32_t hh = h[k];
-        for (int p = 1; t != key[k] && t != kEmptyKey && p < md.max_probe; ++p) {
+        for (int p = 1; t != key[k] && t != kEmptyKey && (p > 1 || sa[k][7] != 0u) &&
+                        p < md.max_probe;
+             ++p) {
           hh = (hh + 1) & mask;
           ld_v8(md.vslots + hh, map_pol, sa[k]);
           ld_v8(reinterpret_cast<const char*>(md.vslots + hh) + 32, map_pol, sb[k]);
@@ -890,169 +901,146 @@ void launch_simple(const LinLaunch& L, int grid, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Software-pipelined per-point kernel (1 neighbour).  Each thread walks its
-// points with a stride of the block size, two points ahead on the source stream
-// and one point ahead on the lookup:
-//   point k+2: position and covariance loads in flight (registers)
-//   point k+1: key computed, first probe of its slot (two 256-bit loads) in flight
-//   point k  : probe resolved (further probes only on a collision), term added
-// so that neither the DRAM latency of the stream nor the L2 latency of the
-// lookup sits on the critical path of a point.
+// Hit-compacting per-warp kernel (1 neighbour).  The lookup phase runs one
+// point per lane; the lanes whose voxel exists push (point, covariance, target-
+// frame residual mu' - q, voxel covariance) as one 80-B entry into their warp's
+// queue in shared memory.  Whenever 32 entries are queued the warp evaluates
+// them with every lane busy, so lanes whose point missed do not cost term
+// arithmetic.  Item constants live in shared memory as in the per-point kernel.
 // ---------------------------------------------------------------------------
-namespace pf {
-#ifndef VGICP_PF_THREADS
-#define VGICP_PF_THREADS 256
+namespace compact {
+#ifndef VGICP_COMPACT_MIN_BLOCKS
+#define VGICP_COMPACT_MIN_BLOCKS 3
 #endif
-constexpr int kThreads = VGICP_PF_THREADS;
-#ifndef VGICP_PF_MIN_BLOCKS
-#define VGICP_PF_MIN_BLOCKS 2
-#endif
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kQueue = 64;  // entries per warp (< 32 left after a drain + at most 32 pushed)
 
-struct Pt {
-  float x, y, z;
-  float2 c01, c23, c45;
-};
-__device__ __forceinline__ void load_pt(const SrcDesc& sd, int p, Pt& d) {
-  const float* pt = sd.pts + 3 * (int64_t)p;
-  d.x = __ldg(pt);
-  d.y = __ldg(pt + 1);
-  d.z = __ldg(pt + 2);
-  const float2* cv = reinterpret_cast<const float2*>(sd.covs + 6 * (int64_t)p);
-  d.c01 = __ldg(cv);
-  d.c23 = __ldg(cv + 1);
-  d.c45 = __ldg(cv + 2);
+__device__ __forceinline__ void eval_entry(float* acc, const float* R, const float4* E) {
+  const float4 e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4];
+  const float c[6] = {e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
+  add_term_t(acc, R, e0.x, e0.y, e0.z, c, e2.y, e2.z, e2.w, e3, e4);
 }
 
-// First probe of a point's lookup, issued ahead of its use.
-struct Probe {
-  uint32_t a[8], b[8];
-  unsigned long long key;
-  uint32_t h;
-  bool live;  // key in range (else a miss without any load)
-};
-__device__ __forceinline__ void issue_probe(const MapDesc& md, uint32_t mask, int kx, int ky,
-                                            int kz, uint64_t pol, Probe& pr) {
-  pr.live = key_in_range(kx) && key_in_range(ky) && key_in_range(kz);
-  pr.key = pack_key(kx, ky, kz);
-  pr.h = hash_key(kx, ky, kz) & mask;
-  if (pr.live) {
-    const VSlot* t = md.vslots + pr.h;
-    ld_v8(t, pol, pr.a);
-    ld_v8(reinterpret_cast<const char*>(t) + 32, pol, pr.b);
-  }
-}
-// Resolves a probe: on a hit returns the global voxel id and fills the record.
-__device__ __forceinline__ int resolve_probe(const MapDesc& md, uint32_t mask, uint64_t pol,
-                                             Probe& pr, float4& r0, float4& r1, float4& r2) {
-  if (!pr.live) return -1;
-  uint32_t h = pr.h;
-  for (int p = 0; p < md.max_probe; ++p) {
-    if (p > 0) {
-      h = (h + 1) & mask;
-      const VSlot* t = md.vslots + h;
-      ld_v8(t, pol, pr.a);
-      ld_v8(reinterpret_cast<const char*>(t) + 32, pol, pr.b);
-    }
-    const unsigned long long k = slot_key(pr.a);
-    if (k == pr.key) {
-      r0 = make_float4(__uint_as_float(pr.a[4]), __uint_as_float(pr.a[5]),
-                       __uint_as_float(pr.a[6]), 0.f);
-      r1 = make_float4(__uint_as_float(pr.b[0]), __uint_as_float(pr.b[1]),
-                       __uint_as_float(pr.b[2]), __uint_as_float(pr.b[3]));
-      r2 = make_float4(__uint_as_float(pr.b[4]), __uint_as_float(pr.b[5]), 0.f, 0.f);
-      return (int)pr.a[2];
-    }
-    if (k == kEmptyKey) return -1;
-  }
-  return -1;
-}
-
-__global__ void __launch_bounds__(kThreads, VGICP_PF_MIN_BLOCKS)
-    linearize_pf_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ float red[kThreads / 32][kAcc];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
+__global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
+    linearize_compact_kernel(const __grid_constant__ LinLaunch L) {
+  __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
+  __shared__ float red[kWarps][kAcc];
+  __shared__ ItemConst ic;
   __shared__ int next_item;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t pol = policy_evict_last_l();
+  float4* Q = queue[warp];
+
   for (int it = blockIdx.x; it < L.n_items;) {
     int pair, begin, end;
     tma::item_bounds(L, it, pair, begin, end);
-    const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-    Pose32 P;
+    if (threadIdx.x == 0) {
+      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
+      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
-    P.t[0] = pd->t[0];
-    P.t[1] = pd->t[1];
-    P.t[2] = pd->t[2];
-    P.tmax = pd->tmax;
-    const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-    const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-    const uint32_t mask = *md.vmask;
-    const uint64_t pol = policy_evict_last_l();
-    uint32_t vbase = 0;
-    if (L.corr_out) vbase = *md.vbase;
+      for (int k = 0; k < 9; ++k) ic.R[k] = pd->R[k];
+      ic.t[0] = pd->t[0];
+      ic.t[1] = pd->t[1];
+      ic.t[2] = pd->t[2];
+      ic.tmax = pd->tmax;
+      ic.inv_r = md.inv_r;
+      ic.margin_scale = md.margin_scale;
+      ic.mask = *md.vmask;
+      ic.vslots = md.vslots;
+      ic.pts = sd.pts;
+      ic.covs = sd.covs;
+      ic.pd = pd;
+      ic.r = md.r;
+      ic.max_probe = md.max_probe;
+    }
+    __syncthreads();
 
     float acc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
+    int qn = 0;  // queued entries (warp-uniform)
+    const int n = end - begin;
 
-    const int stride = blockDim.x;
-    int p = begin + threadIdx.x;
-    Pt cur, nxt;
-    Probe pr;
-    float qx = 0.f, qy = 0.f, qz = 0.f;
-    if (p < end) {
-      load_pt(sd, p, cur);
-      qx = fmaf(P.R[0], cur.x, fmaf(P.R[1], cur.y, fmaf(P.R[2], cur.z, P.t[0])));
-      qy = fmaf(P.R[3], cur.x, fmaf(P.R[4], cur.y, fmaf(P.R[5], cur.z, P.t[1])));
-      qz = fmaf(P.R[6], cur.x, fmaf(P.R[7], cur.y, fmaf(P.R[8], cur.z, P.t[2])));
-      int kx, ky, kz;
-      source_key(P, pd, md, cur.x, cur.y, cur.z, qx, qy, qz, kx, ky, kz);
-      if (L.qkey_out) {
-        L.qkey_out[3 * (int64_t)p + 0] = kx;
-        L.qkey_out[3 * (int64_t)p + 1] = ky;
-        L.qkey_out[3 * (int64_t)p + 2] = kz;
-      }
-      issue_probe(md, mask, kx, ky, kz, pol, pr);
-    }
-    if (p + stride < end) load_pt(sd, p + stride, nxt);
-
-    for (; p < end; p += stride) {
-      // stream: point k+2
-      Pt nn;
-      const bool has_nn = p + 2 * stride < end;
-      if (has_nn) load_pt(sd, p + 2 * stride, nn);
-      // lookup: point k+1
-      Probe pn;
-      float nqx = 0.f, nqy = 0.f, nqz = 0.f;
-      const bool has_n = p + stride < end;
-      if (has_n) {
-        nqx = fmaf(P.R[0], nxt.x, fmaf(P.R[1], nxt.y, fmaf(P.R[2], nxt.z, P.t[0])));
-        nqy = fmaf(P.R[3], nxt.x, fmaf(P.R[4], nxt.y, fmaf(P.R[5], nxt.z, P.t[1])));
-        nqz = fmaf(P.R[6], nxt.x, fmaf(P.R[7], nxt.y, fmaf(P.R[8], nxt.z, P.t[2])));
-        int kx, ky, kz;
-        source_key(P, pd, md, nxt.x, nxt.y, nxt.z, nqx, nqy, nqz, kx, ky, kz);
-        if (L.qkey_out) {
-          L.qkey_out[3 * (int64_t)(p + stride) + 0] = kx;
-          L.qkey_out[3 * (int64_t)(p + stride) + 1] = ky;
-          L.qkey_out[3 * (int64_t)(p + stride) + 2] = kz;
+    for (int base = warp * 32; base < n; base += kThreads) {
+      const int p = begin + base + lane;
+      bool hit = false;
+      float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+      float2 c01, c23, c45;
+      float4 a1, a2;
+      if (p < end) {
+        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+        const float4 g3 = lds_f4(&ic.tmax);
+        uint64_t vs, ps, cs, pds;
+        lds_2ptr(&ic.vslots, vs, ps);
+        lds_2ptr(&ic.covs, cs, pds);
+        const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
+        x = __ldg(pt + 0);
+        y = __ldg(pt + 1);
+        z = __ldg(pt + 2);
+        const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
+                                                           6 * (int64_t)p);
+        c01 = __ldg(cv + 0);
+        c23 = __ldg(cv + 1);
+        c45 = __ldg(cv + 2);
+        const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
+        const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
+        const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
+        const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
+        const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
+        const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
+        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+        const bool ax = (rx < m) | (rx > 1.0f - m);
+        const bool ay = (ry < m) | (ry > 1.0f - m);
+        const bool az = (rz < m) | (rz > 1.0f - m);
+        int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
+        if (ax | ay | az) {
+          const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+          MapDesc mr;
+          mr.r = ic.r;
+          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
         }
-        issue_probe(md, mask, kx, ky, kz, pol, pn);
+        MapDesc md;
+        md.vslots = reinterpret_cast<const VSlot*>(vs);
+        md.max_probe = ic.max_probe;
+        float4 a0;
+        const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
+        hit = vid >= 0;
+        tx = a0.x - qx;
+        ty = a0.y - qy;
+        tz = a0.z - qz;
       }
-      // point k
-      float4 a0, a1, a2;
-      const int vid = resolve_probe(md, mask, pol, pr, a0, a1, a2);
-      if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-      if (vid >= 0) {
-        const float c[6] = {cur.c01.x, cur.c01.y, cur.c23.x, cur.c23.y, cur.c45.x, cur.c45.y};
-        add_term(acc, P, cur.x, cur.y, cur.z, c, qx, qy, qz, a0, a1, a2);
+      const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+      if (hit) {
+        float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
+        E[0] = make_float4(x, y, z, c01.x);
+        E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
+        E[2] = make_float4(c45.y, tx, ty, tz);
+        E[3] = a1;
+        E[4] = a2;
       }
-      cur = nxt;
-      qx = nqx;
-      qy = nqy;
-      qz = nqz;
-      pr = pn;
-      if (has_nn) nxt = nn;
+      if (lane == 0) acc[28] += (float)__popc(hm);
+      qn += __popc(hm);
+      __syncwarp();
+      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
+        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+        const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+        eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
+        qn -= 32;
+        __syncwarp();
+      }
     }
+    if (lane < qn) {  // drain the partially filled queue
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+      eval_entry(acc, R, Q + 5 * lane);
+    }
+    __syncwarp();
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -1068,225 +1056,15 @@ __global__ void __launch_bounds__(kThreads, VGICP_PF_MIN_BLOCKS)
     if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
     __syncthreads();
     if (threadIdx.x < kAcc) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)red[w][threadIdx.x];
-      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
-    }
-    it = next_item;  // read between the two barriers; rewritten only after the second
-    __syncthreads();
-  }
-}
-}  // namespace pf
-
-// ---------------------------------------------------------------------------
-// Pipelined per-warp kernel (1 neighbour).  Each warp walks 32-point chunks of
-// the CTA's work item with a software pipeline:
-//   chunk k+2: point data loads in flight (registers)
-//   chunk k+1: key computed, first probe of its slot (two 256-bit loads) in flight
-//   chunk k  : probes resolved; hits pushed to a per-warp queue in shared memory
-//              (point and voxel Gaussian, 80 B per entry)
-// and whenever 32 hits are queued, the warp evaluates them with every lane busy.
-// The lookups and the stream are both a full iteration ahead of their use.
-// ---------------------------------------------------------------------------
-namespace pipe {
-constexpr int kWarps = 6;
-constexpr int kThreads = kWarps * 32;
-constexpr int kQueue = 64;  // entries per warp (< 32 after a drain + at most 32 pushed)
-
-struct Chunk {  // one point per lane
-  float x, y, z;
-  float c[6];
-  bool valid;
-};
-
-__device__ __forceinline__ void load_chunk(const SrcDesc& sd, int64_t p, bool valid, Chunk& ch) {
-  ch.valid = valid;
-  if (valid) {
-    const float* pt = sd.pts + 3 * p;
-    ch.x = __ldg(pt);
-    ch.y = __ldg(pt + 1);
-    ch.z = __ldg(pt + 2);
-    const float2* cv = reinterpret_cast<const float2*>(sd.covs + 6 * p);
-    const float2 a = __ldg(cv), b = __ldg(cv + 1), c = __ldg(cv + 2);
-    ch.c[0] = a.x; ch.c[1] = a.y; ch.c[2] = b.x; ch.c[3] = b.y; ch.c[4] = c.x; ch.c[5] = c.y;
-  } else {
-    ch.x = ch.y = ch.z = 0.f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) ch.c[k] = 0.f;
-  }
-}
-
-struct Probe {
-  unsigned long long key;
-  uint32_t h;
-  int kx, ky, kz;
-  bool live;
-  uint32_t a[8], b[8];
-};
-
-__device__ __forceinline__ void start_probe(const Pose32& P, const PairDesc* pd, const MapDesc& md,
-                                            uint32_t mask, uint64_t pol, const Chunk& ch,
-                                            Probe& pr) {
-  pr.kx = pr.ky = pr.kz = kKeyMin - 1;
-  pr.live = false;
-  if (ch.valid) {
-    const float qx = fmaf(P.R[0], ch.x, fmaf(P.R[1], ch.y, fmaf(P.R[2], ch.z, P.t[0])));
-    const float qy = fmaf(P.R[3], ch.x, fmaf(P.R[4], ch.y, fmaf(P.R[5], ch.z, P.t[1])));
-    const float qz = fmaf(P.R[6], ch.x, fmaf(P.R[7], ch.y, fmaf(P.R[8], ch.z, P.t[2])));
-    source_key(P, pd, md, ch.x, ch.y, ch.z, qx, qy, qz, pr.kx, pr.ky, pr.kz);
-    pr.live = key_in_range(pr.kx) && key_in_range(pr.ky) && key_in_range(pr.kz);
-  }
-  pr.key = pr.live ? pack_key(pr.kx, pr.ky, pr.kz) : kEmptyKey;
-  pr.h = hash_key(pr.kx, pr.ky, pr.kz) & mask;
-  if (pr.live) {
-    ld_v8(md.vslots + pr.h, pol, pr.a);
-    ld_v8(reinterpret_cast<const char*>(md.vslots + pr.h) + 32, pol, pr.b);
-  } else {
-    pr.a[0] = pr.a[1] = 0xFFFFFFFFu;
-  }
-}
-
-// Resolve a probe (further probes are rare); returns the global voxel id or -1.
-__device__ __forceinline__ int finish_probe(const MapDesc& md, uint32_t mask, uint64_t pol,
-                                            Probe& pr) {
-  if (!pr.live) return -1;
-  unsigned long long t = slot_key(pr.a);
-  uint32_t hh = pr.h;
-  for (int p = 1; t != pr.key && t != kEmptyKey && p < md.max_probe; ++p) {
-    hh = (hh + 1) & mask;
-    ld_v8(md.vslots + hh, pol, pr.a);
-    ld_v8(reinterpret_cast<const char*>(md.vslots + hh) + 32, pol, pr.b);
-    t = slot_key(pr.a);
-  }
-  return t == pr.key ? (int)pr.a[2] : -1;
-}
-
-__global__ void __launch_bounds__(kThreads, 2) linearize_pipe_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
-  __shared__ float red[kWarps][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint64_t pol = policy_evict_last_l();
-  float4* Q = queue[warp];
-  __shared__ int next_item;
-
-  for (int it = blockIdx.x; it < L.n_items;) {
-    int pair, b, e;
-    tma::item_bounds(L, it, pair, b, e);
-    const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-    Pose32 P;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) P.R[k] = pd->R[k];
-    P.t[0] = pd->t[0];
-    P.t[1] = pd->t[1];
-    P.t[2] = pd->t[2];
-    P.tmax = pd->tmax;
-    const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-    const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-    const uint32_t mask = *md.vmask;
-    uint32_t vbase = 0;
-    if (L.corr_out) vbase = *md.vbase;
-
-    float acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
-    int qn = 0;  // queued hits (warp-uniform)
-
-    const int nchunks = (e - b + 31) >> 5;
-    // chunk sequence of this warp: warp, warp + kWarps, ...
-    auto chunk_point = [&](int j) -> int64_t { return (int64_t)b + 32 * (int64_t)(warp + j * kWarps) + lane; };
-    auto chunk_exists = [&](int j) -> bool { return warp + j * kWarps < nchunks; };
-
-    Chunk nxt, cur, pnd;
-    Probe pcur, ppnd;
-    load_chunk(sd, chunk_point(0), chunk_exists(0) && chunk_point(0) < e, cur);
-    load_chunk(sd, chunk_point(1), chunk_exists(1) && chunk_point(1) < e, nxt);
-    start_probe(P, pd, md, mask, pol, cur, pcur);
-
-    for (int j = 0; chunk_exists(j); ++j) {
-      // rotate: chunk j is resolved now; chunk j+1 gets its probe; chunk j+2 loads
-      pnd = cur;
-      ppnd = pcur;
-      cur = nxt;
-      load_chunk(sd, chunk_point(j + 2), chunk_exists(j + 2) && chunk_point(j + 2) < e, nxt);
-      start_probe(P, pd, md, mask, pol, cur, pcur);
-
-      const int vid = finish_probe(md, mask, pol, ppnd);
-      if (L.corr_out || L.qkey_out) {
-        const int64_t p = chunk_point(j);
-        if (pnd.valid) {
-          if (L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-          if (L.qkey_out) {
-            L.qkey_out[3 * p + 0] = ppnd.kx;
-            L.qkey_out[3 * p + 1] = ppnd.ky;
-            L.qkey_out[3 * p + 2] = ppnd.kz;
-          }
-        }
-      }
-      const bool hit = vid >= 0;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
-      if (hit) {
-        float4* E = Q + 5 * (qn + __popc(m & lt_mask));
-        E[0] = make_float4(pnd.x, pnd.y, pnd.z, pnd.c[0]);
-        E[1] = make_float4(pnd.c[1], pnd.c[2], pnd.c[3], pnd.c[4]);
-        E[2] = make_float4(pnd.c[5], __uint_as_float(ppnd.a[4]), __uint_as_float(ppnd.a[5]),
-                           __uint_as_float(ppnd.a[6]));
-        E[3] = make_float4(__uint_as_float(ppnd.b[0]), __uint_as_float(ppnd.b[1]),
-                           __uint_as_float(ppnd.b[2]), __uint_as_float(ppnd.b[3]));
-        E[4] = make_float4(__uint_as_float(ppnd.b[4]), __uint_as_float(ppnd.b[5]), 0.f, 0.f);
-      }
-      if (lane == 0) acc[28] += (float)__popc(m);
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
-        const float4* E = Q + 5 * (qn - 32 + lane);
-        const float4 e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4];
-        const float c[6] = {e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
-        const float qx = fmaf(P.R[0], e0.x, fmaf(P.R[1], e0.y, fmaf(P.R[2], e0.z, P.t[0])));
-        const float qy = fmaf(P.R[3], e0.x, fmaf(P.R[4], e0.y, fmaf(P.R[5], e0.z, P.t[1])));
-        const float qz = fmaf(P.R[6], e0.x, fmaf(P.R[7], e0.y, fmaf(P.R[8], e0.z, P.t[2])));
-        add_term(acc, P, e0.x, e0.y, e0.z, c, qx, qy, qz, make_float4(e2.y, e2.z, e2.w, 0.f),
-                 e3, make_float4(e4.x, e4.y, 0.f, 0.f));
-        acc[28] -= 1.0f;  // add_term counts an inlier; hits were counted at the push
-        qn -= 32;
-        __syncwarp();
-      }
-    }
-    // drain the partially filled queue
-    if (lane < qn) {
-      const float4* E = Q + 5 * lane;
-      const float4 e0 = E[0], e1 = E[1], e2 = E[2], e3 = E[3], e4 = E[4];
-      const float c[6] = {e0.w, e1.x, e1.y, e1.z, e1.w, e2.x};
-      const float qx = fmaf(P.R[0], e0.x, fmaf(P.R[1], e0.y, fmaf(P.R[2], e0.z, P.t[0])));
-      const float qy = fmaf(P.R[3], e0.x, fmaf(P.R[4], e0.y, fmaf(P.R[5], e0.z, P.t[1])));
-      const float qz = fmaf(P.R[6], e0.x, fmaf(P.R[7], e0.y, fmaf(P.R[8], e0.z, P.t[2])));
-      add_term(acc, P, e0.x, e0.y, e0.z, c, qx, qy, qz, make_float4(e2.y, e2.z, e2.w, 0.f), e3,
-               make_float4(e4.x, e4.y, 0.f, 0.f));
-      acc[28] -= 1.0f;
-    }
-    __syncwarp();
-
-    // reduce: warp reduce-scatter, then binary64 across warps
-    tma::rs_step<16>(acc, lane);
-    tma::rs_step<8>(acc, lane);
-    tma::rs_step<4>(acc, lane);
-    tma::rs_step<2>(acc, lane);
-    tma::rs_step<1>(acc, lane);
-    red[warp][lane] = acc[0];
-    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
-    __syncthreads();
-    if (warp == 0 && lane < kAcc) {
       double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) t += (double)red[w][lane];
-      L.partials[(int64_t)it * kPartialStride + lane] = t;
+      for (int w = 0; w < kWarps; ++w) t += (double)red[w][threadIdx.x];
+      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = t;
     }
     it = next_item;  // read between the two barriers; rewritten only after the second
     __syncthreads();
   }
 }
-
-}  // namespace pipe
+}  // namespace compact
 
 // One warp per pair: lane k sums term k over the pair's items in order.
 __global__ void reduce_kernel(const double* __restrict__ partials, const int2* __restrict__ span,
@@ -1337,9 +1115,9 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  if (neighbours != 27 && variant == 4) return device_sm_count() * VGICP_PF_MIN_BLOCKS;
   if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
-  return device_sm_count() * (variant == 3 ? 2 : VGICP_MIN_BLOCKS);
+  if (variant == 3) return device_sm_count() * VGICP_COMPACT_MIN_BLOCKS;
+  return device_sm_count() * VGICP_MIN_BLOCKS;
 }
 
 int launch_linearize(const LinLaunch& L, cudaStream_t st) {
@@ -1363,10 +1141,11 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
+  } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
+    compact::linearize_compact_kernel<<<grid, compact::kThreads, 0, st>>>(L);
   } else if (variant == 3) {
-    pipe::linearize_pipe_kernel<<<grid, pipe::kThreads, 0, st>>>(L);
-  } else if (variant == 4) {
-    pf::linearize_pf_kernel<<<grid, pf::kThreads, 0, st>>>(L);
+    launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
+
   } else {
     static bool attr_set[64] = {false};
     int dev = 0;

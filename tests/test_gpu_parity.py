@@ -267,7 +267,7 @@ def test_pose_validation(dev):
         api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 1]], T[None])
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_kernel_variants_match_oracle(dev, variant):
     tp, tc, sp, sc, T, r = cases.room()
     vm = api.VoxelMap.build(cu(tp), cu(tc), r)
@@ -280,7 +280,7 @@ def test_kernel_variants_match_oracle(dev, variant):
     check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}")
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_map_as_source(dev, variant):
     """A map's own (voxel-grouped) cloud as the source gives the same factor as the
     original cloud, within tolerance, and matches the oracle."""
