@@ -11,10 +11,14 @@
 //   scan      voxel id = number of first points before it (so voxels are
 //             numbered in order of first appearance, map by map)
 //   assign    per first point: voxel count, key; slot.vid <- voxel id
-//   scan      voxel offsets into the point list
+//   sort      per map chunk: the voxels in Morton order of their keys (rank)
+//   scan      offsets of the voxels' point lists, in rank order
 //   scatter   per point: append its index to its voxel's list
-//   finalize  per voxel: sort its list, sum means and covariances in binary64
-//             in ascending point index, divide by N, round to float32
+//   finalize  per voxel, in rank order: sort its list, sum means and
+//             covariances (exactly, else in binary64 in ascending point index),
+//             divide by N, round to float32; copy the points into the voxel-
+//             grouped cloud (the lists laid end to end)
+//   lookup    per map: lookup table (inline records) from the finished voxels
 // The result is deterministic and bit-identical to the binary64 definition
 // rounded once to float32.
 #include <cuda_runtime.h>
@@ -43,6 +47,18 @@ __device__ __forceinline__ int find_map(const int64_t* __restrict__ off, int32_t
   return lo;
 }
 
+// find_map for the points of one warp, which are consecutive: the first active
+// lane searches, the others walk forward from its map (a warp spans few maps).
+__device__ __forceinline__ int find_map_warp(const int64_t* __restrict__ off, int32_t n_maps,
+                                             int64_t i) {
+  const unsigned am = __activemask();
+  const int leader = __ffs(am) - 1;
+  int m = ((int)(threadIdx.x & 31) == leader) ? find_map(off, n_maps, i) : 0;
+  m = __shfl_sync(am, m, leader);
+  while (m + 1 < n_maps && __ldg(off + m + 1) <= i) ++m;
+  return m;
+}
+
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
   atomicCAS(status, 0, code);
 }
@@ -66,7 +82,7 @@ __global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
                               int32_t* status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int m = find_map(point_off, n_maps, i);
+    const int m = find_map_warp(point_off, n_maps, i);
     const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
     const int kx = axis_key_target(__ldg(pts + 3 * i + 0), inv_r, r);
     const int ky = axis_key_target(__ldg(pts + 3 * i + 1), inv_r, r);
@@ -113,7 +129,7 @@ __global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_
     const uint32_t s = pt_slot[i];
     uint32_t f = 0;
     if (s != kNoSlot) {
-      const int m = find_map(point_off, n_maps, i);
+      const int m = find_map_warp(point_off, n_maps, i);
       const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
       f = (slots[s].vid == li) ? 1u : 0u;
     }
@@ -146,24 +162,29 @@ __global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __r
 }
 
 __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot,
-                               const Slot* __restrict__ slots, const uint32_t* __restrict__ voff,
-                               uint32_t* vfill, uint32_t* __restrict__ plist) {
+                               const Slot* __restrict__ slots, const uint32_t* __restrict__ vrank,
+                               const uint32_t* __restrict__ goff, uint32_t* vfill,
+                               uint32_t* __restrict__ plist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = pt_slot[i];
     if (s == kNoSlot) continue;
     const uint32_t v = slots[s].vid;
-    const uint32_t pos = voff[v] + atomicAdd(vfill + v, 1u);
+    const uint32_t pos = goff[vrank[v]] + atomicAdd(vfill + v, 1u);
     plist[pos] = (uint32_t)i;
   }
 }
 
-// Per-voxel binary64 sums in ascending point index.  A CTA takes 256 consecutive
-// voxels, whose point lists are one contiguous segment of plist: the segment is
-// loaded into shared memory (coalesced), each thread sorts its voxel's short
-// list there, the sorted segment is written back (the grouping step reads it),
-// and the sums gather the points four at a time.  Segments longer than the
-// staging buffer fall back to sorting in global memory.
+// Per-voxel sums and the grouped cloud.  A CTA takes 256 consecutive ranks,
+// whose point lists are one contiguous segment of plist:
+//   1. the segment is loaded into shared memory (coalesced) and each thread
+//      sorts its voxel's short list there by point index (segments longer than
+//      the staging buffer sort in place in global memory);
+//   2. point-parallel: every thread gathers points of the segment and writes
+//      them to the grouped cloud at their list positions (balanced, coalesced
+//      writes; the random reads all in flight at once);
+//   3. voxel-parallel: each thread sums its voxel's points from the grouped copy
+//      just written (L2-resident) and writes the voxel record.
 constexpr int kFinThreads = 256;
 constexpr int kFinStage = 6144;  // indices staged per CTA
 
@@ -209,80 +230,89 @@ __device__ __forceinline__ double div_rn(double s, double n, double y) {
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     int64_t n_max, const uint32_t* __restrict__ n_vox, const float* __restrict__ pts,
     const float* __restrict__ covs, const uint32_t* __restrict__ vcount,
-    const uint32_t* __restrict__ voff, uint32_t* __restrict__ plist, float4* __restrict__ recs,
-    const uint32_t* __restrict__ vrank, const uint32_t* __restrict__ goff,
-    float* __restrict__ gpts, float* __restrict__ gcovs) {
+    const uint32_t* __restrict__ vorder, const uint32_t* __restrict__ goff,
+    uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gpts, float* gcovs) {
   __shared__ uint32_t stage[kFinStage];
   const int64_t V = min((int64_t)*n_vox, n_max);
-  for (int64_t v0 = (int64_t)blockIdx.x * kFinThreads; v0 < V; v0 += (int64_t)gridDim.x * kFinThreads) {
-    const int64_t v1 = min(V, v0 + kFinThreads);
-    const uint32_t seg0 = voff[v0];
-    const uint32_t seg1 = voff[v1 - 1] + vcount[v1 - 1];
-    const bool staged = seg1 - seg0 <= (uint32_t)kFinStage;
-    const int64_t v = v0 + threadIdx.x;
-    const bool mine = v < v1;
+  for (int64_t r0 = (int64_t)blockIdx.x * kFinThreads; r0 < V; r0 += (int64_t)gridDim.x * kFinThreads) {
+    const int64_t r1 = min(V, r0 + kFinThreads);
+    const uint32_t seg0 = goff[r0];
+    const uint32_t seg1 = goff[r1 - 1] + vcount[vorder[r1 - 1]];
+    const uint32_t len = seg1 - seg0;
+    const bool staged = len <= (uint32_t)kFinStage;
+    const int64_t r = r0 + threadIdx.x;
+    const bool mine = r < r1;
+    const uint32_t v = mine ? vorder[r] : 0u;
     const uint32_t c = mine ? vcount[v] : 0u;
-    const uint32_t o = mine ? voff[v] : 0u;
+    const uint32_t o = mine ? goff[r] : 0u;
+    // 1. sort the lists by point index
     if (staged) {
-      for (uint32_t i = threadIdx.x; i < seg1 - seg0; i += kFinThreads) stage[i] = plist[seg0 + i];
+      for (uint32_t i = threadIdx.x; i < len; i += kFinThreads) stage[i] = plist[seg0 + i];
       __syncthreads();
       if (mine) insertion_sort(stage + (o - seg0), c);
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < seg1 - seg0; i += kFinThreads) plist[seg0 + i] = stage[i];
     } else if (mine) {
       insertion_sort(plist + o, c);
     }
+    __syncthreads();
+    // 2. gather into the grouped cloud
+    const uint32_t* lst = staged ? stage : plist + seg0;
+    for (uint32_t i = threadIdx.x; i < len; i += kFinThreads) {
+      const int64_t j = lst[i];
+      const float x = __ldg(pts + 3 * j), y = __ldg(pts + 3 * j + 1), z = __ldg(pts + 3 * j + 2);
+      const float2* cv = reinterpret_cast<const float2*>(covs + 6 * j);
+      const float2 c0 = __ldg(cv), c1 = __ldg(cv + 1), c2 = __ldg(cv + 2);
+      const int64_t d = (int64_t)seg0 + i;
+      gpts[3 * d + 0] = x;
+      gpts[3 * d + 1] = y;
+      gpts[3 * d + 2] = z;
+      float2* gc = reinterpret_cast<float2*>(gcovs + 6 * d);
+      gc[0] = c0;
+      gc[1] = c1;
+      gc[2] = c2;
+    }
+    __syncthreads();  // the CTA's global writes are visible to the CTA after this
+    // 3. sums from the grouped copy (plain loads: written by this kernel)
     if (mine) {
-      const uint32_t* Lst = staged ? stage + (o - seg0) : plist + o;
-      const int64_t dst0 = goff[vrank[v]];
       float hi[9], lo[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) hi[k] = lo[k] = 0.0f;
       bool exact = true;
       for (uint32_t a = 0; a < c; ++a) {
-        const int64_t j = Lst[a];
+        const int64_t d = (int64_t)o + a;
         float f[9];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) f[k] = __ldg(pts + 3 * j + k);
-        const float2* cv = reinterpret_cast<const float2*>(covs + 6 * j);
-        const float2 c0 = __ldg(cv), c1 = __ldg(cv + 1), c2 = __ldg(cv + 2);
+        for (int k = 0; k < 3; ++k) f[k] = gpts[3 * d + k];
+        const float2* gc = reinterpret_cast<const float2*>(gcovs + 6 * d);
+        const float2 c0 = gc[0], c1 = gc[1], c2 = gc[2];
         f[3] = c0.x; f[4] = c0.y; f[5] = c1.x; f[6] = c1.y; f[7] = c2.x; f[8] = c2.y;
-        // the voxel-grouped, spatially ordered copy of the cloud
-        const int64_t d = dst0 + a;
-        gpts[3 * d + 0] = f[0];
-        gpts[3 * d + 1] = f[1];
-        gpts[3 * d + 2] = f[2];
-        float2* gc = reinterpret_cast<float2*>(gcovs + 6 * d);
-        gc[0] = c0;
-        gc[1] = c1;
-        gc[2] = c2;
 #pragma unroll
         for (int k = 0; k < 9; ++k) df_add(hi[k], lo[k], f[k], exact);
       }
-      double s[9];
+      double sum[9];
       if (exact) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s[k] = __dadd_rn((double)hi[k], (double)lo[k]);  // exact
+        for (int k = 0; k < 9; ++k) sum[k] = __dadd_rn((double)hi[k], (double)lo[k]);  // exact
       } else {
-        // binary64 sum in ascending point index (rare: large dynamic range)
+        // binary64 sum in ascending point index (the grouped order; rare: large
+        // dynamic range)
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s[k] = 0.0;
+        for (int k = 0; k < 9; ++k) sum[k] = 0.0;
         for (uint32_t a = 0; a < c; ++a) {
-          const int64_t j = Lst[a];
+          const int64_t d = (int64_t)o + a;
 #pragma unroll
-          for (int k = 0; k < 3; ++k) s[k] = __dadd_rn(s[k], (double)__ldg(pts + 3 * j + k));
+          for (int k = 0; k < 3; ++k) sum[k] = __dadd_rn(sum[k], (double)gpts[3 * d + k]);
 #pragma unroll
-          for (int k = 0; k < 6; ++k) s[3 + k] = __dadd_rn(s[3 + k], (double)__ldg(covs + 6 * j + k));
+          for (int k = 0; k < 6; ++k) sum[3 + k] = __dadd_rn(sum[3 + k], (double)gcovs[6 * d + k]);
         }
       }
       const double N = (double)c;
       const double y = __drcp_rn(N);
-      float r[9];
+      float q[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) r[k] = __double2float_rn(div_rn(s[k], N, y));
-      recs[3 * v + 0] = make_float4(r[0], r[1], r[2], __uint_as_float(c));
-      recs[3 * v + 1] = make_float4(r[3], r[4], r[5], r[6]);
-      recs[3 * v + 2] = make_float4(r[7], r[8], 0.0f, 0.0f);
+      for (int k = 0; k < 9; ++k) q[k] = __double2float_rn(div_rn(sum[k], N, y));
+      recs[3 * v + 0] = make_float4(q[0], q[1], q[2], __uint_as_float(c));
+      recs[3 * v + 1] = make_float4(q[3], q[4], q[5], q[6]);
+      recs[3 * v + 2] = make_float4(q[7], q[8], 0.0f, 0.0f);
     }
     __syncthreads();  // the stage is reused by the next batch
   }
@@ -306,17 +336,26 @@ __device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
 }
 
 // One CTA per (map, chunk): bitonic sort of the chunk's voxels by Morton code in
-// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order.
+// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order
+// and vorder[rank] = v.
 constexpr int kSortThreads = 1024;
 __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
-    const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank) {
+    const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank,
+    uint32_t* __restrict__ vorder) {
   extern __shared__ unsigned long long sk[];
   const int m = chunks[blockIdx.x].x;
   const uint32_t V = vbase[m + 1] - vbase[m];
   const uint32_t lo = (uint32_t)chunks[blockIdx.x].y * kMortonChunk;
   if (lo >= V) return;
   const uint32_t cnt = min((uint32_t)kMortonChunk, V - lo);
+#ifdef VGICP_NO_MORTON
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    vrank[vbase[m] + lo + i] = vbase[m] + lo + i;
+    vorder[vbase[m] + lo + i] = vbase[m] + lo + i;
+  }
+  return;
+#endif
   uint32_t N = 1;
   while (N < cnt) N <<= 1;
   const uint32_t first = vbase[m] + lo;
@@ -339,8 +378,11 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
       __syncthreads();
     }
   }
-  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
-    vrank[first + (uint32_t)(sk[i] & 0xFFFFFFFFull)] = first + i;
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const uint32_t v = first + (uint32_t)(sk[i] & 0xFFFFFFFFull);
+    vrank[v] = first + i;
+    vorder[first + i] = v;
+  }
 }
 
 __global__ void rank_counts_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
@@ -372,8 +414,10 @@ __global__ void vslot_init_kernel(const int64_t* __restrict__ slot_base,
   VSlot* t = vslots + slot_base[m];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
   {
-    t[i].key = kEmptyKey;
-    t[i].spill = 0u;
+    // the whole first 32-B sector (key = empty, spill = 0): no read-modify-write
+    asm volatile("st.global.v8.b32 [%0], {%1, %1, %2, %2, %2, %2, %2, %2};" ::"l"(t + i),
+                 "r"(0xFFFFFFFFu), "r"(0u)
+                 : "memory");
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) vmask[m] = cap - 1u;
 }
@@ -521,10 +565,12 @@ __global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_m
   }
 }
 
+// One thread per element (no grid-stride cap): CTAs are dispatched roughly in
+// index order, so the maps being worked on at any moment are a few consecutive
+// ones whose clouds and tables stay in L2 while their random accesses land.
 int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  int64_t cap = (int64_t)device_sm_count() * 32;
-  return (int)std::max<int64_t>(1, std::min(g, cap));
+  const int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 0x7FFFFFFF));
 }
 
 }  // namespace
@@ -621,16 +667,12 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
     rc = size_lookup_tables(s, st);
     if (rc != VGICP_OK) return rc;
   }
-  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
-  rc = launch_exclusive_scan(s->d_vcount, s->d_voff, n, s->d_num_voxels, s->d_scan_tmp,
-                             s->d_num_valid, st);
-  if (rc != VGICP_OK) return rc;
-  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_voff, s->d_vfill,
-                                         s->d_plist);
-  // Morton order of the voxels (chunks of a map) and the grouped offsets, then the
-  // per-voxel sums, which also write the voxel-grouped copy of the clouds;
-  // d_flag and d_vfill are free scratch at this point
+  // Morton order of the voxels (chunks of a map), the list offsets in that order,
+  // the lists, then the per-voxel sums (which also write the grouped clouds).
+  // d_flag (voxel id per first point) is dead after vbase, d_vfill (first flags)
+  // after assign.
   uint32_t* vrank = s->d_flag;
+  uint32_t* vorder = s->d_voff;
   uint32_t* gcount = s->d_vfill;
   static bool sort_attr = false;
   if (!sort_attr) {
@@ -640,13 +682,19 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
     sort_attr = true;
   }
   morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kMortonChunk, st>>>(
-      s->d_chunks, s->d_vbase, s->d_vkeys, vrank);
-  rank_counts_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_vcount, gcount);
+      s->d_chunks, s->d_vbase, s->d_vkeys, vrank, vorder);
+  // light kernels over voxels (V <= n is on the device): grid-stride, capped grid
+  const int gv = std::min<int>(g, device_sm_count() * 8);
+  rank_counts_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_vcount, gcount);
   VGICP_CUDA_TRY(cudaGetLastError());
-  rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp, nullptr, st);
+  rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp,
+                             s->d_num_valid, st);
   if (rc != VGICP_OK) return rc;
+  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
+  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, vrank, s->d_goff,
+                                         s->d_vfill, s->d_plist);
   finalize_kernel<<<g, kFinThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
-                                             s->d_voff, s->d_plist, s->d_recs, vrank, s->d_goff,
+                                             vorder, s->d_goff, s->d_plist, s->d_recs,
                                              s->d_gpts, s->d_gcovs);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)

@@ -52,12 +52,12 @@ struct MapSet {
   unsigned long long* d_vkeys = nullptr;    // n_total (packed keys by voxel)
   int32_t* d_status = nullptr;              // 1
   // device: build scratch (kept for rebuilds)
-  uint32_t* d_pt_slot = nullptr;  // n_total
-  uint32_t* d_flag = nullptr;     // n_total: first-point flags, then voxel ids
-  uint32_t* d_vcount = nullptr;   // n_total
-  uint32_t* d_voff = nullptr;     // n_total
-  uint32_t* d_vfill = nullptr;    // n_total
-  uint32_t* d_plist = nullptr;    // n_total
+  uint32_t* d_pt_slot = nullptr;  // n_total: build-table slot of each point
+  uint32_t* d_flag = nullptr;     // n_total: voxel id of first points, then rank of each voxel
+  uint32_t* d_vcount = nullptr;   // n_total: points per voxel
+  uint32_t* d_voff = nullptr;     // n_total: voxel at each rank
+  uint32_t* d_vfill = nullptr;    // n_total: first-point flags, counts by rank, list fill
+  uint32_t* d_plist = nullptr;    // n_total: point lists of the voxels, in rank order
   float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
   float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
   uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
