@@ -231,6 +231,43 @@ def oracle_sample(w, budget_s, nthreads, start_pair=0, min_pairs=2):
     return pts_done, time.perf_counter() - t0, done
 
 
+# ---------------------------------------------------------------------------
+# ncu DRAM traffic of the linearize kernel, from the committed profile summary
+# ---------------------------------------------------------------------------
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "linearize_global_map_traffic.txt")
+KERNEL_SOURCES = ["paper_2202_00242_gb300/csrc/vgicp_linearize.cu",
+                  "paper_2202_00242_gb300/csrc/vgicp_device.cuh",
+                  "paper_2202_00242_gb300/csrc/vgicp_internal.h"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(source_points: int):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one linearize launch, scaled
+    to `source_points` from the captured launch, or None when there is no capture
+    of the current kernel sources."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None
+        per_point = float(kv["dram_bytes_per_launch"]) / float(kv["source_points_per_launch"])
+        return per_point * source_points
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -409,7 +446,7 @@ def run_ours(args):
                                                 "autotuned": not (args.tile or args.variant),
                                                 "cuda_graph": True}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(n_pts),
                          "kernel": "linearize (1-neighbour), timed as its graph (status reset + "
                                    "linearize + per-pair reduce)", "kernel_ms": kernel_ms,
                          "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pts,
