@@ -152,6 +152,14 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
 //   0..5   H_ww (00 01 02 11 12 22)      6..14 H_wv (row-major, w rows, v cols)
 //   15..20 H_vv (00 01 02 11 12 22)      21..23 b_w   24..26 b_v   27 err
 //   28     inlier count
+// 1 / x to about 1 ulp (rcp.approx: one instruction; H, b and err are held to
+// 1e-4 relative, many orders above this).  Deterministic.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void add_term_t(float* acc, const float* R, float x, float y, float z,
                                            const float* c, float tx, float ty, float tz,
                                            const float4 r1, const float4 r2) {
@@ -186,7 +194,7 @@ __device__ __forceinline__ void add_term_t(float* acc, const float* R, float x, 
   const float i12 = fmaf(m01, m02, -m00 * m12);
   const float i22 = fmaf(m00, m11, -m01 * m01);
   const float det = fmaf(m00, i00, fmaf(m01, i01, m02 * i02));
-  const float s = __frcp_rn(det);
+  const float s = rcp_approx(det);
   const float w00 = i00 * s, w01 = i01 * s, w02 = i02 * s;
   const float w11 = i11 * s, w12 = i12 * s, w22 = i22 * s;
   // u = W' d'
@@ -675,7 +683,7 @@ __device__ __forceinline__ void eval_term(float* acc, const Pose32& P, float x, 
   const float i12 = fmaf(m01, m02, -m00 * m12);
   const float i22 = fmaf(m00, m11, -m01 * m01);
   const float det = fmaf(m00, i00, fmaf(m01, i01, m02 * i02));
-  const float sc = __frcp_rn(det);
+  const float sc = rcp_approx(det);
   const float u0 = fmaf(i00, d0, fmaf(i01, d1, i02 * d2)) * sc;
   const float u1 = fmaf(i01, d0, fmaf(i11, d1, i12 * d2)) * sc;
   const float u2 = fmaf(i02, d0, fmaf(i12, d1, i22 * d2)) * sc;
