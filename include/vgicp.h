@@ -234,6 +234,19 @@ int vgicp_se3_right_jacobian(const double* xi, double* J);
 int vgicp_pose_mul(const double* A, const double* B, double* C);
 int vgicp_solve6(const double* H, const double* b, double lambda, double* xi);
 
+/* Overlap rate (Sec. III-D: the fraction of a frame's points that fall within a
+ * voxel of the other frame; keyframes, submaps and global factors are created
+ * from it, Sec. III-D to III-F).  For each pair, inliers[p] (device, n_pairs) =
+ * the number of source points whose transformed voxel is occupied in the target
+ * map; the rate is inliers[p] / n_src.  Same factor description as
+ * vgicp_linearize_batched; lookups only (the source covariances are not read).
+ * opts: tile, grid; neighbours must be 0 or 1.  A nonzero device status gives
+ * inliers = -1. */
+int vgicp_overlap_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                          int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                          const double* poses, int64_t* inliers, const vgicp_lin_opts* opts,
+                          vgicp_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Admission: factor sets larger than device memory (host-only planning).      */
 /* ------------------------------------------------------------------------ */

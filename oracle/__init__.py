@@ -148,6 +148,18 @@ class Linearization:
     d: np.ndarray | None = None      # (n, 3)
 
 
+def overlap(vmap: VoxelMap, src_points, T) -> float:
+    """Overlap rate (Sec. III-D): the fraction of the source points whose
+    transformed position falls in an occupied voxel of the map, i.e. the inlier
+    count of the 1-neighbour linearization over n (the covariances do not enter
+    the lookup; identity covariances are passed)."""
+    p = _f32(src_points, 3)
+    if p.shape[0] == 0:
+        return 0.0
+    eye = np.tile(np.array([1, 0, 0, 1, 0, 1], dtype=np.float32), (p.shape[0], 1))
+    return linearize(vmap, p, eye, T, nthreads=0).inliers / p.shape[0]
+
+
 def linearize(vmap: VoxelMap, src_points, src_covs, T, neighbours: int = 1,
               nthreads: int = 1, debug: bool = False) -> Linearization:
     """Linearise one factor (Eqs. 2-3) at T = T_target_source (4x4, binary64)."""

@@ -370,6 +370,53 @@ def evaluate_batched(maps, sources, pairs, poses, mode=GRADIENT, neighbours=1, t
     return out[:, :6], out[:, 6], inl
 
 
+def overlap_batched(maps, sources, pairs, poses, tile=0, stream=None):
+    """Overlap rate of each factor (Sec. III-D): the fraction of the source
+    points that fall in an occupied voxel of the target map at the pose.
+    Returns (rate (P,) float64, inliers (P,) int64), device."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0]
+    poses = _pose_array(poses, P)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    inl = torch.empty(P, dtype=torch.int64, device=dev)
+    clouds = make_clouds(sources)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    opts = LinOpts(1, int(tile), 0, 0, None, None, None, None)
+    check(_lib.load().vgicp_overlap_batched(arr, len(maps), clouds, len(sources),
+                                            pairs.ctypes.data_as(ctypes.c_void_p), P,
+                                            poses.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.c_void_p(inl.data_ptr()), ctypes.byref(opts),
+                                            _stream_ptr(stream)))
+    sizes = [s.n if isinstance(s, VoxelMap) else int(s[0].shape[0]) for s in sources]
+    n = torch.tensor([sizes[int(c)] for c in pairs[:, 1]], dtype=torch.float64, device=dev)
+    return inl.double() / n.clamp(min=1.0), inl
+
+
+def relative_poses(world_poses, pairs) -> np.ndarray:
+    """T_target_source = T_j^-1 T_i for each pair (j, i) of world poses (binary64)."""
+    W = np.asarray(world_poses, dtype=np.float64).reshape(-1, 4, 4)
+    pairs = np.asarray(pairs).reshape(-1, 2)
+    inv = np.linalg.inv(W)
+    return np.stack([inv[j] @ W[i] for j, i in pairs]) if len(pairs) else np.zeros((0, 4, 4))
+
+
+def factor_candidates(maps, sources, world_poses, threshold=0.05, tile=0, stream=None):
+    """Global-mapping factor creation (Sec. III-F): every ordered pair (target j,
+    source i), i != j, whose overlap rate at T_j^-1 T_i reaches ``threshold``.
+    ``sources[i]`` is submap i's cloud (or its map), ``world_poses[i]`` its pose.
+    Returns (pairs (K, 2) int32 host, rates (K,) float64 host)."""
+    W = np.asarray(world_poses, dtype=np.float64).reshape(-1, 4, 4)
+    C = len(maps)
+    jj, ii = np.meshgrid(np.arange(C), np.arange(C), indexing="ij")
+    sel = jj != ii
+    pairs = np.stack([jj[sel], ii[sel]], 1).astype(np.int32)
+    poses = relative_poses(W, pairs)
+    rate, _ = overlap_batched(maps, sources, pairs, poses, tile=tile, stream=stream)
+    rate = rate.cpu().numpy()
+    keep = rate >= threshold
+    return pairs[keep], rate[keep]
+
+
 def gauss_newton(vmap: VoxelMap, points: torch.Tensor, covs: torch.Tensor, T0, max_iters=30,
                  tol=1e-9, damping=0.0, neighbours=1):
     """Minimise one factor's cost over T = T_target_source: linearize on the GPU

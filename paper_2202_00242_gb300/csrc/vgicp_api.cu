@@ -483,6 +483,16 @@ int vgicp_evaluate_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_c
                       stream, mode);
 }
 
+int vgicp_overlap_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                          int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                          const double* poses, int64_t* inliers, const vgicp_lin_opts* opts,
+                          vgicp_stream_t stream) {
+  if (opts && opts->neighbours != 0 && opts->neighbours != 1)
+    return set_error(VGICP_ERR_INVALID_ARG, "the overlap rate uses the 1-neighbour lookup");
+  return batched_impl(maps, n_maps, sources, n_sources, pairs, n_pairs, poses, nullptr, inliers,
+                      opts, stream, 4);
+}
+
 static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
                         int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                         const double* poses, double* out, int64_t* inliers,
@@ -490,7 +500,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
   g_error.clear();
   if (n_pairs < 0) return set_error(VGICP_ERR_INVALID_ARG, "negative n_pairs");
   if (n_pairs == 0) return VGICP_OK;
-  if (!maps || n_maps <= 0 || !sources || n_sources <= 0 || !pairs || !poses || !out || !inliers)
+  if (!maps || n_maps <= 0 || !sources || n_sources <= 0 || !pairs || !poses ||
+      (!out && mode != 4) || !inliers)
     return set_error(VGICP_ERR_INVALID_ARG, "null argument");
   if (n_pairs > INT32_MAX / 2) return set_error(VGICP_ERR_INVALID_ARG, "too many pairs");
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;

@@ -707,12 +707,16 @@ __device__ __forceinline__ void eval_term(float* acc, const Pose32& P, float x, 
   acc[28] += 1.0f;
 }
 
+// MODE 0: linearization (H, b, err); 1-3: cost / gradient / exact gradient;
+// 4: overlap (the inlier count only: no term arithmetic, no covariance reads).
 template <int MODE>
 __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float y, float z,
                                      const float* c, float qx, float qy, float qz,
                                      const float4 r0, const float4 r1, const float4 r2) {
   if (MODE == 0)
     add_term(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
+  else if (MODE == 4)
+    acc[28] += 1.0f;
   else
     eval_term<MODE>(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
 }
@@ -1088,6 +1092,10 @@ __global__ void reduce_kernel(const double* __restrict__ partials, const int2* _
   if (lane < kAcc)
     for (int32_t it = a; it < b; ++it) s += partials[(int64_t)it * kPartialStride + lane];
   if (status && *status != 0) s = __longlong_as_double(0x7FF8000000000000ll);  // NaN
+  if (mode == 4) {  // overlap: the inlier count only
+    if (lane == 28) inliers[pair] = (status && *status != 0) ? -1 : (int64_t)llrint(s);
+    return;
+  }
   if (mode != 0) {  // gradient (6) and err (1)
     if (lane < 7) out[pair * 7 + lane] = s;
     if (lane == 28) inliers[pair] = (status && *status != 0) ? -1 : (int64_t)llrint(s);
@@ -1143,7 +1151,8 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     } else {
       if (L.mode == 1) launch_simple<1, 1>(L, grid, st);
       else if (L.mode == 2) launch_simple<1, 2>(L, grid, st);
-      else launch_simple<1, 3>(L, grid, st);
+      else if (L.mode == 3) launch_simple<1, 3>(L, grid, st);
+      else launch_simple<1, 4>(L, grid, st);
     }
   } else if (L.neighbours == 27) {
     launch_simple<27, 0>(L, grid, st);

@@ -333,3 +333,46 @@ def test_plan_graph_autotune_matches_oracle_and_batched(dev):
         ref = oracle.linearize(omaps[j], sp, sc, poses2[p], nthreads=0)
         check_factor(c.out[p], c.inliers[p], ref, f"plan pair {p}")
     plan.close()
+
+
+def test_overlap_rate_matches_oracle_and_linearize(dev):
+    """Overlap rate (Sec. III-D) of every factor equals the oracle's and the
+    linearization's inlier count over n, exactly."""
+    w = cases.workload_with_knn_covs("outdoor", seed=33, n_submaps=10, neighbours=3)
+    C = len(w.clouds.offsets) - 1
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    srcs = [(pts[w.clouds.offsets[c]:w.clouds.offsets[c + 1]],
+             covs[w.clouds.offsets[c]:w.clouds.offsets[c + 1]]) for c in range(C)]
+    rate, inl = api.overlap_batched(maps, srcs, w.pairs, w.poses, tile=4096)
+    lin = api.linearize_batched(maps, srcs, w.pairs, w.poses, tile=4096)
+    assert torch.equal(inl, lin.inliers)
+    rate_m, inl_m = api.overlap_batched(maps, maps, w.pairs, w.poses)
+    assert torch.equal(inl_m, inl)  # the grouped copy holds the same points
+    for p, (j, i) in enumerate(w.pairs):
+        tp, tc = w.clouds.cloud(j)
+        sp, _ = w.clouds.cloud(i)
+        assert float(rate[p]) == oracle.overlap(oracle.build_voxelmap(tp, tc, w.resolution), sp,
+                                                w.poses[p])
+
+
+def test_factor_candidates_threshold(dev):
+    """Global-map factor creation (Sec. III-F): all ordered pairs whose overlap at
+    the relative world pose reaches the threshold, and no others."""
+    w = cases.workload_with_knn_covs("outdoor", seed=34, n_submaps=8, neighbours=2)
+    C = len(w.clouds.offsets) - 1
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    pairs, rates = api.factor_candidates(maps, maps, w.world_poses, threshold=0.05)
+    got = {(int(j), int(i)) for j, i in pairs}
+    assert (rates >= 0.05).all() and len(got) > 0
+    omaps = [oracle.build_voxelmap(*w.clouds.cloud(j), w.resolution) for j in range(C)]
+    for j in range(C):
+        for i in range(C):
+            if i == j:
+                continue
+            T = api.relative_poses(w.world_poses, [[j, i]])[0]
+            o = oracle.overlap(omaps[j], w.clouds.cloud(i)[0], T)
+            assert ((j, i) in got) == (o >= 0.05), (j, i, o)

@@ -398,3 +398,27 @@ def test_empty_and_all_miss(oracle_lib):
     far[:3, 3] += 1000.0
     m = oracle_lib.linearize(vm, sp, sc, far)
     assert m.inliers == 0 and m.err == 0 and not m.H.any()
+
+
+def test_overlap_rate_pins(oracle_lib):
+    """Overlap rate (Sec. III-D): a cloud against its own map at the identity is
+    1 (every point lies in its own voxel); far away it is 0; in general it is the
+    brute-force fraction of transformed points whose key is a map key."""
+    import oracle
+    rng = np.random.default_rng(8)
+    pts = (rng.random((500, 3)) * 4.0 - 2.0).astype(np.float32)
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (500, 1))
+    vm = oracle.build_voxelmap(pts, covs, 0.5)
+    assert oracle.overlap(vm, pts, np.eye(4)) == 1.0
+    far = np.eye(4)
+    far[:3, 3] = 100.0
+    assert oracle.overlap(vm, pts, far) == 0.0
+    src = (rng.random((300, 3)) * 6.0 - 3.0).astype(np.float32)
+    T = np.eye(4)
+    T[:3, 3] = [0.3, -0.2, 0.1]
+    q = src.astype(np.float64) + T[:3, 3]
+    keys = {tuple(k) for k in np.floor(q / 0.5).astype(np.int64)}
+    mk = {tuple(k) for k in vm.keys}
+    hits = sum(tuple(k) in mk for k in np.floor(q / 0.5).astype(np.int64))
+    assert len(keys) > 1
+    assert oracle.overlap(vm, src, T) == hits / 300
