@@ -234,6 +234,16 @@ int vgicp_se3_right_jacobian(const double* xi, double* J);
 int vgicp_pose_mul(const double* A, const double* B, double* C);
 int vgicp_solve6(const double* H, const double* b, double lambda, double* xi);
 
+/* Binary form of a matching-cost factor, which constrains the two poses T_i
+ * (source) and T_j (target) (Sec. III-A).  Input: the factor's H (6x6), b (6)
+ * in the right perturbation xi of T = T_j^-1 T_i (as vgicp_linearize returns them)
+ * and T (4x4).  With right perturbations of the world poses, T_i <- T_i Exp(d_i)
+ * and T_j <- T_j Exp(d_j), xi = d_i - Ad(T^-1) d_j to first order, so over
+ * [d_i; d_j]: H2 = A^T H A (12x12) and b2 = A^T b (12) with A = [I, -Ad(T^-1)]
+ * (Ad of [omega; v] twists).  All host binary64, row-major. */
+int vgicp_binary_factor(const double* H, const double* b, const double* T, double* H2,
+                        double* b2);
+
 /* Overlap rate (Sec. III-D: the fraction of a frame's points that fall within a
  * voxel of the other frame; keyframes, submaps and global factors are created
  * from it, Sec. III-D to III-F).  For each pair, inliers[p] (device, n_pairs) =

@@ -54,6 +54,7 @@ SIGNATURES = {
     "vgicp_se3_right_jacobian": (ctypes.c_int, [P, P]),
     "vgicp_pose_mul": (ctypes.c_int, [P, P, P]),
     "vgicp_solve6": (ctypes.c_int, [P, P, f64, P]),
+    "vgicp_binary_factor": (ctypes.c_int, [P, P, P, P, P]),
     "vgicp_overlap_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
                                              P, i64, P, P, ctypes.POINTER(LinOpts), P]),
     "vgicp_voxelmap_bytes": (i64, [i64, ctypes.POINTER(MapOpts)]),

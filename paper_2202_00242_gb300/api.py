@@ -345,6 +345,58 @@ def solve6(H, b, damping: float = 0.0) -> np.ndarray:
     return x
 
 
+def binary_factor(H, b, T):
+    """12x12 H2 and 12 b2 of a factor over [delta_i; delta_j], the right
+    perturbations of the source and target world poses (binary64, host)."""
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(6, 6))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(6))
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(4, 4))
+    H2 = np.empty((12, 12))
+    b2 = np.empty(12)
+    check(_lib.load().vgicp_binary_factor(H.ctypes.data_as(ctypes.c_void_p),
+                                          b.ctypes.data_as(ctypes.c_void_p),
+                                          T.ctypes.data_as(ctypes.c_void_p),
+                                          H2.ctypes.data_as(ctypes.c_void_p),
+                                          b2.ctypes.data_as(ctypes.c_void_p)))
+    return H2, b2
+
+
+def optimize_pose_graph(maps, sources, pairs, world_poses, fixed=0, iters=10, damping=1e-6,
+                        tile=0, stream=None):
+    """Gauss-Newton over the world poses of submaps joined by matching-cost
+    factors (the global-mapping graph of Sec. III-F without IMU factors): every
+    iteration re-linearizes all factors in one batched launch (Sec. III-A),
+    expands each to its two poses, and solves the normal equations on the host
+    in binary64 with pose ``fixed`` held as the gauge.  Returns (poses (C, 4, 4),
+    total cost per iteration)."""
+    W = np.array(world_poses, dtype=np.float64).reshape(-1, 4, 4)
+    C = W.shape[0]
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    hist = []
+    for _ in range(int(iters)):
+        poses = relative_poses(W, pairs)
+        out = linearize_batched(maps, sources, pairs, poses, tile=tile,
+                                stream=stream).out.cpu().numpy()
+        Hg = np.zeros((6 * C, 6 * C))
+        bg = np.zeros(6 * C)
+        hist.append(float(out[:, 42].sum()))
+        for p, (j, i) in enumerate(pairs):
+            H2, b2 = binary_factor(out[p, :36], out[p, 36:42], poses[p])
+            idx = np.r_[6 * i:6 * i + 6, 6 * j:6 * j + 6]
+            Hg[np.ix_(idx, idx)] += H2
+            bg[idx] += b2
+        keep = np.ones(6 * C, dtype=bool)
+        keep[6 * fixed:6 * fixed + 6] = False
+        A = Hg[np.ix_(keep, keep)]
+        A = A + damping * np.diag(np.diag(A))
+        d = np.zeros(6 * C)
+        d[keep] = -np.linalg.solve(A, bg[keep])
+        for c in range(C):
+            if c != fixed:
+                W[c] = W[c] @ se3_exp(d[6 * c:6 * c + 6])
+    return W, hist
+
+
 COST, GRADIENT, EXACT_GRADIENT = 1, 2, 3
 
 

@@ -144,6 +144,47 @@ int vgicp_pose_mul(const double* A, const double* B, double* C) {
   return VGICP_OK;
 }
 
+int vgicp_binary_factor(const double* H, const double* b, const double* T, double* H2,
+                        double* b2) {
+  if (!H || !b || !T || !H2 || !b2) return vgicp::set_error(VGICP_ERR_INVALID_ARG, "null argument");
+  // A = [I, -Ad(T^-1)] maps [delta_i; delta_j] to xi.  With T^-1 = (R^T, -R^T t)
+  // and xi = [omega; v]: Ad(T^-1) = [[R^T, 0], [[-R^T t]x R^T, R^T]].
+  double Rt[9], ti[3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Rt[3 * r + c] = T[4 * c + r];
+  for (int r = 0; r < 3; ++r)
+    ti[r] = -(Rt[3 * r] * T[3] + Rt[3 * r + 1] * T[7] + Rt[3 * r + 2] * T[11]);
+  double TX[9], TXR[9];
+  hat3(ti, TX);
+  mm3(TX, Rt, TXR);
+  double A[6 * 12] = {0};
+  for (int r = 0; r < 6; ++r) A[12 * r + r] = 1.0;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      A[12 * r + 6 + c] = -Rt[3 * r + c];            // omega <- omega_j
+      A[12 * (3 + r) + 9 + c] = -Rt[3 * r + c];      // v <- v_j
+      A[12 * (3 + r) + 6 + c] = -TXR[3 * r + c];     // v <- omega_j
+    }
+  double HA[6 * 12];
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 12; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += H[6 * r + k] * A[12 * k + c];
+      HA[12 * r + c] = acc;
+    }
+  for (int r = 0; r < 12; ++r) {
+    for (int c = 0; c < 12; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += A[12 * k + r] * HA[12 * k + c];
+      H2[12 * r + c] = acc;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < 6; ++k) acc += A[12 * k + r] * b[k];
+    b2[r] = acc;
+  }
+  return VGICP_OK;
+}
+
 int vgicp_solve6(const double* H, const double* b, double lambda, double* xi) {
   if (!H || !b || !xi) return vgicp::set_error(VGICP_ERR_INVALID_ARG, "null argument");
   double A[36], L[36] = {0};

@@ -157,3 +157,49 @@ def test_gauss_newton_matches_oracle_trajectory(dev):
     T_conv, _ = api.gauss_newton(vm, cu(sp), cu(sc), np.eye(4), max_iters=40, tol=1e-9)
     rot, tr = se3.pose_error(T_conv, T_true)
     assert rot < 0.1 and tr < 0.01, (rot, tr)
+
+
+def test_pose_graph_gauss_newton_converges(dev):  # noqa: F811
+    """Global-map optimization over submap world poses (Sec. III-F, matching-cost
+    factors only): the first iteration's normal equations match those built from
+    the oracle's linearizations, and the perturbed poses converge to the true
+    ones within the bias of the voxelized cost."""
+    from paper_2202_00242_gb300 import api, synth
+    w = synth.with_surface_covariances(synth.outdoor_submaps(
+        seed=41, n_submaps=8, n_min=20000, n_max=30000, neighbours=3, size_dist="uniform"))
+    C = len(w.clouds.offsets) - 1
+    pts = torch.from_numpy(w.clouds.points).cuda()
+    covs = torch.from_numpy(w.clouds.covs).cuda()
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w.resolution)
+    maps[0].status()
+    srcs = [(pts[w.clouds.offsets[c]:w.clouds.offsets[c + 1]],
+             covs[w.clouds.offsets[c]:w.clouds.offsets[c + 1]]) for c in range(C)]
+    rng = np.random.default_rng(5)
+    W0 = np.array(w.world_poses)
+    for c in range(1, C):
+        W0[c] = W0[c] @ api.se3_exp(np.r_[rng.normal(0, np.radians(1.0), 3), rng.normal(0, 0.1, 3)])
+    # first-iteration normal equations against the oracle's factors
+    poses = api.relative_poses(W0, w.pairs)
+    lin = api.linearize_batched(maps, srcs, w.pairs, poses).out.cpu().numpy()
+    Hg = np.zeros((6 * C, 6 * C))
+    Ho = np.zeros((6 * C, 6 * C))
+    for p, (j, i) in enumerate(w.pairs):
+        ref = oracle.linearize(oracle.build_voxelmap(*w.clouds.cloud(j), w.resolution),
+                               *w.clouds.cloud(i), poses[p], nthreads=0)
+        idx = np.r_[6 * i:6 * i + 6, 6 * j:6 * j + 6]
+        Hg[np.ix_(idx, idx)] += api.binary_factor(lin[p, :36], lin[p, 36:42], poses[p])[0]
+        Ho[np.ix_(idx, idx)] += api.binary_factor(ref.H, ref.b, poses[p])[0]
+    assert np.linalg.norm(Hg - Ho) <= 1e-4 * np.linalg.norm(Ho)
+
+    def errors(W):  # (max translation error [m], max rotation error [deg])
+        e = [se3.pose_error(np.linalg.inv(W[0]) @ W[c],
+                            np.linalg.inv(w.world_poses[0]) @ w.world_poses[c])
+             for c in range(1, C)]
+        return max(t for _, t in e), max(r for r, _ in e)
+
+    t0, r0 = errors(W0)
+    W, hist = api.optimize_pose_graph(maps, srcs, w.pairs, W0, fixed=0, iters=8)
+    t1, r1 = errors(W)
+    assert hist[-1] < hist[0]
+    assert t1 < 0.3 * t0 and t1 < 0.05, (t0, t1)
+    assert r1 < 0.3 * r0, (r0, r1)

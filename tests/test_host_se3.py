@@ -60,3 +60,34 @@ def test_solve6_and_pose_mul(api):
     T1 = api.se3_exp(rng.normal(size=6))
     T2 = api.se3_exp(rng.normal(size=6))
     np.testing.assert_allclose(api.pose_mul(T1, T2), T1 @ T2, atol=1e-14)
+
+
+def _se3_log(T):
+    """Twist [omega; v] of a 4x4 rigid transform via the matrix logarithm."""
+    X = np.real(scipy.linalg.logm(T))
+    return np.array([X[2, 1], X[0, 2], X[1, 0], X[0, 3], X[1, 3], X[2, 3]])
+
+
+def test_binary_factor_against_finite_differences(api):
+    """The 12x12 form over the world-pose perturbations: A (d xi / d [d_i; d_j]) by
+    central differences of Log(T^-1 T(d)) with T(d) = (T_j Exp(d_j))^-1 T_i Exp(d_i),
+    then H2 = A^T H A and b2 = A^T b."""
+    rng = np.random.default_rng(3)
+    Ti = api.se3_exp(rng.normal(size=6) * [0.5, 0.5, 0.5, 3, 3, 3])
+    Tj = api.se3_exp(rng.normal(size=6) * [0.5, 0.5, 0.5, 3, 3, 3])
+    T = np.linalg.inv(Tj) @ Ti
+    M = rng.normal(size=(6, 6))
+    H = M @ M.T + np.eye(6)
+    b = rng.normal(size=6)
+    h = 1e-6
+    A = np.zeros((6, 12))
+    for k in range(12):
+        d = np.zeros(12)
+        d[k] = h
+        Tp = np.linalg.inv(Tj @ api.se3_exp(d[6:])) @ (Ti @ api.se3_exp(d[:6]))
+        Tm = np.linalg.inv(Tj @ api.se3_exp(-d[6:])) @ (Ti @ api.se3_exp(-d[:6]))
+        A[:, k] = (_se3_log(np.linalg.inv(T) @ Tp) - _se3_log(np.linalg.inv(T) @ Tm)) / (2 * h)
+    H2, b2 = api.binary_factor(H, b, T)
+    assert np.allclose(H2, A.T @ H @ A, rtol=1e-6, atol=1e-6 * np.abs(H2).max())
+    assert np.allclose(b2, A.T @ b, rtol=1e-6, atol=1e-6 * np.abs(b2).max())
+    assert np.allclose(H2, H2.T)
