@@ -59,6 +59,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip the batched vs per-factor comparison")
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--workload", choices=["global", "room", "corridor", "differentiable", "large"],
+                    default="global",
+                    help="global (default): the global-map factor set; the others measure the "
+                         "single-factor, odometry-window, autograd and large-map workloads")
+    ap.add_argument("--resolution", type=float, default=0.0,
+                    help="voxel resolution of the corridor workload (0: 0.25 m)")
     return ap.parse_args(argv)
 
 
@@ -503,10 +509,143 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the other workloads (one GPU; each line uses the same metric)
+# ---------------------------------------------------------------------------
+
+def _timed(torch, fn, steps, warmup):
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_workload(args):
+    import torch
+    from paper_2202_00242_gb300 import _lib, api, autograd, build, synth
+    build.build()
+    lib = _lib.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    K = args.steps if args.steps != 200 else {"room": 200, "corridor": 200, "differentiable": 20,
+                                               "large": 2}[args.workload]
+    extra = {"covariances": "surface-normal Gaussians, eigenvalues (1, 1, 1e-3)"}
+    if args.workload == "room":
+        w = synth.with_surface_covariances(synth.config_room())
+        tp, tc = w.clouds.cloud(0)
+        sp, sc = w.clouds.cloud(1)
+        tpd, tcd = torch.from_numpy(tp).to(dev), torch.from_numpy(tc).to(dev)
+        spd, scd = torch.from_numpy(sp).to(dev), torch.from_numpy(sc).to(dev)
+        vm = api.VoxelMap.build(tpd, tcd, w.resolution)
+        out = torch.empty(api.RESULT_SIZE, dtype=torch.float64, device=dev)
+        inl = torch.empty((), dtype=torch.int64, device=dev)
+        T = w.poses[0]
+
+        def step():
+            api.rebuild_voxelmaps([vm], tpd, tcd)
+            api.linearize(vm, spd, scd, T, out=out, inliers=inl)
+        n_pts = sp.shape[0]
+        name = "room_single_factor_8192x8192_r0.5"
+        extra["step"] = "rebuild the target voxel map + one single-factor linearization"
+    elif args.workload == "corridor":
+        r = args.resolution or 0.25
+        w = synth.with_surface_covariances(synth.config_corridor(resolution=r))
+        Kf = len(w.clouds.offsets) - 2
+        off = w.clouds.offsets
+        pts = torch.from_numpy(w.clouds.points).to(dev)
+        covs = torch.from_numpy(w.clouds.covs).to(dev)
+        kp, kc = pts[:off[Kf]].contiguous(), covs[:off[Kf]].contiguous()
+        maps = api.build_voxelmaps(kp, kc, off[:Kf + 1], r)
+        src = [(pts[off[Kf]:off[Kf + 1]], covs[off[Kf]:off[Kf + 1]])]
+        pairs = np.stack([np.arange(Kf), np.zeros(Kf, np.int64)], 1)
+        plan = api.Plan(maps, src, pairs)
+        plan.autotune(w.poses)
+
+        def step():
+            api.rebuild_voxelmaps(maps, kp, kc)
+            plan.execute(w.poses)
+        n_pts = Kf * int(off[Kf + 1] - off[Kf])
+        name = f"corridor_window_1scan_vs_{Kf}keyframes_20000pts_r{r:g}"
+        extra["step"] = "rebuild the 10 keyframe maps + batched linearization (CUDA graph)"
+    elif args.workload == "differentiable":
+        w = synth.with_surface_covariances(synth.config_differentiable())
+        off = w.clouds.offsets
+        C = len(off) - 1
+        pts = torch.from_numpy(w.clouds.points).to(dev)
+        covs = torch.from_numpy(w.clouds.covs).to(dev)
+        maps = api.build_voxelmaps(pts, covs, off, w.resolution)
+        srcs = [(pts[off[c]:off[c + 1]], covs[off[c]:off[c + 1]]) for c in range(C)]
+        fs = autograd.FactorSet(maps, srcs, w.pairs, w.poses)
+        xi = torch.zeros((w.pairs.shape[0], 6), dtype=torch.float64, requires_grad=True)
+
+        def step():
+            xi.grad = None
+            fs.cost(xi).sum().backward()
+        n_pts = int(w.source_points_per_step)
+        name = f"differentiable_{w.pairs.shape[0]}pairs_20k-50k_r{w.resolution:g}"
+        extra["step"] = ("forward (cost kernel) + backward (gradient kernel, J_r^T on the host) "
+                         "of the autograd Function over all factors; points counted once")
+    else:  # large
+        w = synth.with_surface_covariances(synth.config_large_map(n_submaps=args.submaps
+                                                                   if args.submaps != 500
+                                                                   else 2000))
+        budget = 24 << 30
+        state = {}
+
+        def step():
+            state["r"] = api.linearize_admitted(w.clouds.points, w.clouds.covs, w.clouds.offsets,
+                                                w.pairs, w.poses, w.resolution, budget=budget,
+                                                neighbours=27)
+        n_pts = int(w.source_points_per_step)
+        name = (f"large_map_{len(w.clouds.offsets) - 1}submaps_x100k_{w.pairs.shape[0]}pairs"
+                f"_r0.5_27neighbours")
+        extra["step"] = ("admission batches under a 24 GB budget: per batch, upload the "
+                         "submaps from host memory, build their maps, one batched "
+                         "27-neighbour linearization")
+        extra["inputs"] = "host memory (7.2 GB of clouds, uploaded inside every step)"
+    launches0 = lib.vgicp_launch_count()
+    clocks = ClockSampler(gpu_uuid(torch))
+    clocks.start()
+    ms = _timed(torch, step, K, args.warmup)
+    clk = clocks.stop()
+    if args.workload == "large":
+        extra["admission_batches"] = int(state["r"][2])
+    launches = lib.vgicp_launch_count() - launches0
+    value = n_pts / (ms / 1e3)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = BYTES_PER_POINT * n_pts / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "source pts/s", "n_gpus": 1, "steps": K,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scenes; no dataset available)",
+        "config": dict({"workload": name, "source_points_per_step": n_pts}, **extra),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole step (36 B per source point over the step time)"},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "global":
+        run_workload(args)
     else:
         run_ours(args)
 
