@@ -59,7 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip the batched vs per-factor comparison")
     ap.add_argument("--seed", type=int, default=3)
-    ap.add_argument("--workload", choices=["global", "room", "corridor", "differentiable", "large"],
+    ap.add_argument("--workload", choices=["global", "room", "corridor", "differentiable", "large",
+                                           "covariances"],
                     default="global",
                     help="global (default): the global-map factor set; the others measure the "
                          "single-factor, odometry-window, autograd and large-map workloads")
@@ -535,7 +536,7 @@ def run_workload(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     K = args.steps if args.steps != 200 else {"room": 200, "corridor": 200, "differentiable": 20,
-                                               "large": 2}[args.workload]
+                                               "large": 2, "covariances": 20}[args.workload]
     extra = {"covariances": "surface-normal Gaussians, eigenvalues (1, 1, 1e-3)"}
     if args.workload == "room":
         w = synth.with_surface_covariances(synth.config_room())
@@ -592,6 +593,19 @@ def run_workload(args):
         name = f"differentiable_{w.pairs.shape[0]}pairs_20k-50k_r{w.resolution:g}"
         extra["step"] = ("forward (cost kernel) + backward (gradient kernel, J_r^T on the host) "
                          "of the autograd Function over all factors; points counted once")
+    elif args.workload == "covariances":
+        w = synth.config_global_map(n_submaps=args.submaps)
+        pts = torch.from_numpy(w.clouds.points).to(dev)
+        off = w.clouds.offsets
+
+        def step():
+            api.estimate_covariances(pts, offsets=off, k=10, eps=1e-3)
+        n_pts = int(off[-1])
+        name = f"knn_covariances_{len(off) - 1}clouds_{n_pts}pts_k10"
+        extra["step"] = ("k = 10 nearest neighbours (exact, binary64 distances) and the "
+                         "regularised covariance of every point, clouds searched separately")
+        extra["unit_note"] = "points (not source points of factors) per second"
+        extra["covariances"] = "computed by the step"
     else:  # large
         w = synth.with_surface_covariances(synth.config_large_map(n_submaps=args.submaps
                                                                    if args.submaps != 500

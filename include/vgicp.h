@@ -257,6 +257,22 @@ int vgicp_overlap_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cl
                           const double* poses, int64_t* inliers, const vgicp_lin_opts* opts,
                           vgicp_stream_t stream);
 
+/* Point covariances from the k nearest neighbours (Sec. III-C: each point is a
+ * Gaussian whose covariance comes from its neighbouring points), regularised as
+ * in GICP: the sample covariance of the k neighbours (the point itself
+ * included, ties broken by lower index, squared distances formed in binary64)
+ * has its eigenvalues, in decreasing order, replaced by (1, 1, eps).
+ * points: device, the concatenated clouds (offsets: host, n_clouds + 1, from 0,
+ * non-decreasing); neighbours are searched within each cloud.  k in [1, 32];
+ * eps in (0, 1]; cell: grid cell size of the search (0 = per cloud from its
+ * bounding box).  covs_out: device n x 6 (xx xy xz yy yz zz).  nbr_out: optional
+ * device n x k int32, the neighbours in (distance, index) order as cloud-local
+ * indices, -1 past the cloud's size.  Allocates scratch on the stream and
+ * synchronizes it (to report VGICP_ERR_KEY_RANGE / VGICP_ERR_HASH_FULL). */
+int vgicp_estimate_covariances(const float* points, const int64_t* offsets, int32_t n_clouds,
+                               int32_t k, double eps, double cell, int32_t* nbr_out,
+                               float* covs_out, vgicp_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Admission: factor sets larger than device memory (host-only planning).      */
 /* ------------------------------------------------------------------------ */

@@ -422,6 +422,26 @@ def evaluate_batched(maps, sources, pairs, poses, mode=GRADIENT, neighbours=1, t
     return out[:, :6], out[:, 6], inl
 
 
+def estimate_covariances(points: torch.Tensor, offsets=None, k: int = 10, eps: float = 1e-3,
+                         cell: float = 0.0, neighbours: bool = False, stream=None):
+    """Regularised k-nearest-neighbour covariances (Sec. III-C) of each point of
+    the clouds concatenated in ``points`` (device (n, 3) float32; ``offsets``
+    host, default one cloud).  Returns covs (n, 6) float32 device, and with
+    ``neighbours`` also the (n, k) int32 cloud-local neighbour indices."""
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be (n, 3) float32")
+    points = points.contiguous()
+    n = points.shape[0]
+    off = np.ascontiguousarray(np.asarray([0, n] if offsets is None else offsets, dtype=np.int64))
+    covs = torch.empty((n, 6), dtype=torch.float32, device=points.device)
+    nbr = torch.empty((n, k), dtype=torch.int32, device=points.device) if neighbours else None
+    check(_lib.load().vgicp_estimate_covariances(
+        ctypes.c_void_p(points.data_ptr()), off.ctypes.data_as(ctypes.c_void_p), len(off) - 1,
+        int(k), float(eps), float(cell), ctypes.c_void_p(nbr.data_ptr()) if nbr is not None else None,
+        ctypes.c_void_p(covs.data_ptr()), _stream_ptr(stream)))
+    return (covs, nbr) if neighbours else covs
+
+
 def overlap_batched(maps, sources, pairs, poses, tile=0, stream=None):
     """Overlap rate of each factor (Sec. III-D): the fraction of the source
     points that fall in an occupied voxel of the target map at the pose.
