@@ -273,6 +273,27 @@ int vgicp_estimate_covariances(const float* points, const int64_t* offsets, int3
                                int32_t k, double eps, double cell, int32_t* nbr_out,
                                float* covs_out, vgicp_stream_t stream);
 
+/* Voxel-grid downsampling with timestamp averaging (Sec. III-C: the input
+ * clouds are downsampled by a voxel grid whose voxels average the timestamps
+ * of their points as well as their positions; a point whose time lies far from
+ * its voxel's goes to another, new voxel so the first and last points of a scan
+ * are not fused).  Reading: a point's voxel is floor(p / resolution); the voxel's
+ * reference time is that of its first point (index order); a point whose time
+ * differs from it by more than `split` (e.g. a tenth of the scan duration)
+ * belongs to the voxel's second output voxel.  Output voxels are numbered in
+ * order of first appearance, cloud by cloud; each is the mean of its points'
+ * positions and times (binary64 mean rounded to float32).
+ * points: device n x 3; times: device n or NULL (no split, no times out);
+ * offsets: host n_clouds + 1 (from 0, non-decreasing).  out_points: device,
+ * room for n x 3; out_times: device n or NULL; out_counts: device n or NULL
+ * (points per output voxel); out_offsets: host n_clouds + 1 (cloud c's output
+ * voxels are out_offsets[c] .. out_offsets[c + 1] - 1).  Allocates scratch on
+ * the stream and synchronizes it. */
+int vgicp_downsample(const float* points, const float* times, const int64_t* offsets,
+                     int32_t n_clouds, double resolution, double split, float* out_points,
+                     float* out_times, int32_t* out_counts, int64_t* out_offsets,
+                     vgicp_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Admission: factor sets larger than device memory (host-only planning).      */
 /* ------------------------------------------------------------------------ */

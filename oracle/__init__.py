@@ -81,6 +81,8 @@ def _load():
     lib.oracle_knn_grid.restype = None
     lib.oracle_regularized_covariances.argtypes = [P, i64, i32, P, d, P]
     lib.oracle_regularized_covariances.restype = None
+    lib.oracle_downsample.argtypes = [P, P, i64, d, d, P, P, P]
+    lib.oracle_downsample.restype = i64
     lib.oracle_jacobi_eigen3.argtypes = [P, P, P]
     lib.oracle_jacobi_eigen3.restype = None
     lib.oracle_mat3_inverse.argtypes = [P, P]
@@ -249,6 +251,22 @@ def knn_covariances(points, k: int = 10, eps: float = 1e-3, nthreads: int = 0) -
     """Point covariances from the k nearest neighbours (self included), eigenvalues
     replaced by (1, 1, eps).  Returns (n, 6) binary64."""
     return regularized_covariances(points, knn_grid(points, k, nthreads=nthreads), eps)
+
+
+def downsample(points, times, resolution: float, split: float = 0.0):
+    """Voxel-grid downsampling with timestamp averaging (Sec. III-C): returns
+    (points (V, 3) float32, times (V,) float32 or None, counts (V,) int64), the
+    output voxels in order of first appearance."""
+    p = _f32(points, 3)
+    n = p.shape[0]
+    t = None if times is None else np.ascontiguousarray(times, dtype=np.float32).reshape(n)
+    op = np.empty((max(n, 1), 3), dtype=np.float32)
+    ot = np.empty(max(n, 1), dtype=np.float32) if t is not None else None
+    oc = np.empty(max(n, 1), dtype=np.int64)
+    V = _load().oracle_downsample(_ptr(p), None if t is None else _ptr(t), n, float(resolution),
+                                  float(split), _ptr(op), None if ot is None else _ptr(ot),
+                                  _ptr(oc))
+    return op[:V].copy(), (None if ot is None else ot[:V].copy()), oc[:V].copy()
 
 
 def jacobi_eigen3(A):

@@ -39,6 +39,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <unordered_map>
 #include <vector>
 #ifdef _OPENMP
@@ -50,6 +51,9 @@ namespace {
 struct Key3 {
   int64_t x, y, z;
   bool operator==(const Key3& o) const { return x == o.x && y == o.y && z == o.z; }
+  bool operator<(const Key3& o) const {
+    return x != o.x ? x < o.x : (y != o.y ? y < o.y : z < o.z);
+  }
 };
 struct Key3Hash {
   size_t operator()(const Key3& k) const {
@@ -582,6 +586,52 @@ void oracle_regularized_covariances(const float* pts, int64_t n, int k, const in
     covs[6 * i + 0] = Cr[0]; covs[6 * i + 1] = Cr[1]; covs[6 * i + 2] = Cr[2];
     covs[6 * i + 3] = Cr[4]; covs[6 * i + 4] = Cr[5]; covs[6 * i + 5] = Cr[8];
   }
+}
+
+// Voxel-grid downsampling with timestamp averaging (Sec. III-C).  Points are
+// taken in index order.  A point's voxel is floor(p / r); the voxel's reference
+// time is that of its first point; a point whose time differs from it by more
+// than `split` (the paper's example: a tenth of the scan duration) goes to the
+// voxel's second, separate output voxel, so that the first and last points of a
+// scan are not fused.  Output voxels are numbered in order of first appearance;
+// each holds the binary64 mean of its points' positions and times (sums in
+// index order, then / N), rounded to float32.  times == NULL or split <= 0: no
+// split, no times.  Returns the number of output voxels.
+int64_t oracle_downsample(const float* pts, const float* times, int64_t n, double r, double split,
+                          float* out_pts, float* out_times, int64_t* out_counts) {
+  struct First {
+    int64_t index;
+    double time;
+  };
+  std::unordered_map<Key3, First, Key3Hash> first;
+  std::map<std::pair<Key3, int>, int64_t> id;
+  std::vector<double> sum;  // 4 per output voxel: x, y, z, t
+  std::vector<int64_t> cnt;
+  const bool timed = times != nullptr && split > 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const Key3 k{axis_key(pts[3 * i], r), axis_key(pts[3 * i + 1], r), axis_key(pts[3 * i + 2], r)};
+    const double ti = times ? (double)times[i] : 0.0;
+    auto f = first.find(k);
+    if (f == first.end()) f = first.emplace(k, First{i, ti}).first;
+    const int sub = timed && std::fabs(ti - f->second.time) > split ? 1 : 0;
+    auto g = id.find({k, sub});
+    if (g == id.end()) {
+      g = id.emplace(std::make_pair(k, sub), (int64_t)cnt.size()).first;
+      cnt.push_back(0);
+      sum.insert(sum.end(), {0.0, 0.0, 0.0, 0.0});
+    }
+    const int64_t v = g->second;
+    for (int c = 0; c < 3; ++c) sum[4 * v + c] += pts[3 * i + c];
+    sum[4 * v + 3] += ti;
+    ++cnt[v];
+  }
+  const int64_t V = (int64_t)cnt.size();
+  for (int64_t v = 0; v < V; ++v) {
+    for (int c = 0; c < 3; ++c) out_pts[3 * v + c] = (float)(sum[4 * v + c] / (double)cnt[v]);
+    if (out_times) out_times[v] = (float)(sum[4 * v + 3] / (double)cnt[v]);
+    out_counts[v] = cnt[v];
+  }
+  return V;
 }
 
 // Eigen-decomposition exposed for its own pin (against a library routine).

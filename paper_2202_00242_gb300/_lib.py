@@ -58,6 +58,7 @@ SIGNATURES = {
     "vgicp_overlap_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
                                              P, i64, P, P, ctypes.POINTER(LinOpts), P]),
     "vgicp_estimate_covariances": (ctypes.c_int, [P, P, i32, i32, f64, f64, P, P, P]),
+    "vgicp_downsample": (ctypes.c_int, [P, P, P, i32, f64, f64, P, P, P, P, P]),
     "vgicp_voxelmap_bytes": (i64, [i64, ctypes.POINTER(MapOpts)]),
     "vgicp_admission_schedule": (ctypes.c_int, [P, i32, P, i32, P, i64, i64, i32, P, P]),
     "vgicp_plan_create": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32, P,

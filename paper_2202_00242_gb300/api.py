@@ -422,6 +422,31 @@ def evaluate_batched(maps, sources, pairs, poses, mode=GRADIENT, neighbours=1, t
     return out[:, :6], out[:, 6], inl
 
 
+def downsample(points: torch.Tensor, resolution: float, times: torch.Tensor | None = None,
+               split: float = 0.0, offsets=None, stream=None):
+    """Voxel-grid downsampling with timestamp averaging (Sec. III-C).  Returns
+    (points (V, 3), times (V,) or None, counts (V,) int32, out_offsets (C + 1,)
+    int64 host), the output voxels in order of first appearance per cloud."""
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be (n, 3) float32")
+    points = points.contiguous()
+    n = points.shape[0]
+    off = np.ascontiguousarray(np.asarray([0, n] if offsets is None else offsets, dtype=np.int64))
+    if times is not None:
+        times = times.to(torch.float32).contiguous()
+    op = torch.empty((max(n, 1), 3), dtype=torch.float32, device=points.device)
+    ot = torch.empty(max(n, 1), dtype=torch.float32, device=points.device) if times is not None else None
+    oc = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    oo = np.zeros(len(off), dtype=np.int64)
+    check(_lib.load().vgicp_downsample(
+        ctypes.c_void_p(points.data_ptr()), ctypes.c_void_p(times.data_ptr()) if times is not None else None,
+        off.ctypes.data_as(ctypes.c_void_p), len(off) - 1, float(resolution), float(split),
+        ctypes.c_void_p(op.data_ptr()), ctypes.c_void_p(ot.data_ptr()) if ot is not None else None,
+        ctypes.c_void_p(oc.data_ptr()), oo.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+    V = int(oo[-1])
+    return op[:V], (ot[:V] if ot is not None else None), oc[:V], oo
+
+
 def estimate_covariances(points: torch.Tensor, offsets=None, k: int = 10, eps: float = 1e-3,
                          cell: float = 0.0, neighbours: bool = False, stream=None):
     """Regularised k-nearest-neighbour covariances (Sec. III-C) of each point of

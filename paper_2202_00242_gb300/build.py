@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libvgicp_gb300.so")
 SOURCES = ["vgicp_build.cu", "vgicp_linearize.cu", "vgicp_api.cu", "vgicp_plan.cu",
-           "vgicp_se3.cu", "vgicp_admission.cu", "vgicp_knn.cu"]
+           "vgicp_se3.cu", "vgicp_admission.cu", "vgicp_knn.cu",
+           "vgicp_downsample.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -200,33 +200,6 @@ __device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
   }
 }
 
-// Exact sum of float32 values in a double-float (hi + lo) accumulator: TwoSum
-// (Knuth; Moeller) keeps hi + lo equal to the running sum as long as the one
-// rounding step, lo + e, is exact; that is checked (its own TwoSum error must be
-// 0) and reported through `exact`.  While exact, hi + lo is the exact sum, equal
-// to the binary64 sum in any order, so no ordering is needed for it.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void df_add(float& hi, float& lo, float v, bool& exact) {
-  float t, e, u, e2;
-  two_sum(hi, v, t, e);
-  two_sum(lo, e, u, e2);
-  exact = exact && (e2 == 0.0f);
-  two_sum(t, u, hi, lo);
-}
-
-// Correctly rounded binary64 quotient s / n from the rounded reciprocal and one
-// correction step (Markstein's theorem: with y = RN(1/n) and q = RN(s*y), the
-// residual r = s - q*n is exact under FMA and RN(q + r*y) = RN(s/n)).
-__device__ __forceinline__ double div_rn(double s, double n, double y) {
-  const double q = __dmul_rn(s, y);
-  const double r = __fma_rn(-q, n, s);
-  return __fma_rn(r, y, q);
-}
-
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     int64_t n_max, const uint32_t* __restrict__ n_vox, const float* __restrict__ pts,
     const float* __restrict__ covs, const uint32_t* __restrict__ vcount,

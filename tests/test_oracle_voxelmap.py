@@ -70,3 +70,41 @@ def test_build_counts_sum_and_empty(oracle_lib):
     assert len({tuple(k) for k in vm.keys.tolist()}) == vm.num_voxels
     empty = oracle_lib.build_voxelmap(np.zeros((0, 3), np.float32), np.zeros((0, 6), np.float32), 0.5)
     assert empty.num_voxels == 0
+
+
+def test_downsample_pins(oracle_lib):
+    """Voxel-grid downsampling (Sec. III-C): without a time split it is the voxel
+    map's means and counts; with it, brute-force grouping by (voxel, |t - t_first|
+    > split) in first-appearance order, binary64 means rounded to float32."""
+    import oracle
+    rng = np.random.default_rng(4)
+    pts = (rng.random((400, 3)) * 3.0 - 1.5).astype(np.float32)
+    t = rng.random(400).astype(np.float32) * 0.1
+    covs = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (400, 1))
+    dp, dt, dc = oracle.downsample(pts, None, 0.5)
+    vm = oracle.build_voxelmap(pts, covs, 0.5)
+    assert dt is None
+    assert np.array_equal(dc, vm.counts)
+    assert np.array_equal(dp, vm.means.astype(np.float32))
+    split = 0.01
+    dp, dt, dc = oracle.downsample(pts, t, 0.5, split)
+    groups, order = {}, []
+    first_t = {}
+    for i in range(400):
+        k = tuple(int(v) for v in np.floor(pts[i].astype(np.float64) / 0.5))
+        first_t.setdefault(k, float(t[i]))
+        g = (k, abs(float(t[i]) - first_t[k]) > split)
+        if g not in groups:
+            groups[g] = []
+            order.append(g)
+        groups[g].append(i)
+    assert len(order) == len(dc) > vm.num_voxels
+    for v, g in enumerate(order):
+        idx = groups[g]
+        assert dc[v] == len(idx)
+        s = np.zeros(4)
+        for i in idx:  # binary64 sums in index order
+            s[:3] += pts[i].astype(np.float64)
+            s[3] += float(t[i])
+        assert np.array_equal(dp[v], (s[:3] / len(idx)).astype(np.float32))
+        assert dt[v] == np.float32(s[3] / len(idx))
