@@ -394,28 +394,51 @@ def run_ours(args):
                       "per_factor_launches": {"ms": pf_ms, "value": n_pts / (pf_ms / 1e3),
                                               "launches": 2 * P}}
 
-    # e2e through the public API: pinned host clouds in, results out, every step
+    # e2e through the public API: pinned host clouds in, results out, every step.
+    # Step k+1's clouds are uploaded on a copy stream into the other of two device
+    # buffers while step k rebuilds its maps and linearizes; every upload and
+    # every read-back lies inside the timed region.
     pts_h = torch.from_numpy(w.clouds.points).pin_memory()
     covs_h = torch.from_numpy(w.clouds.covs).pin_memory()
     out_h = torch.empty_like(out, device="cpu").pin_memory()
     inl_h = torch.empty_like(inl, device="cpu").pin_memory()
     E = max(args.e2e_steps, 2)
+    bufs = [(pts, covs), (torch.empty_like(pts), torch.empty_like(covs))]
+    cstream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step():
-        pts.copy_(pts_h, non_blocking=True)
-        covs.copy_(covs_h, non_blocking=True)
-        step()
-        out_h.copy_(out, non_blocking=True)
-        inl_h.copy_(inl, non_blocking=True)
+    def upload(b):
+        cstream.wait_event(freed[b])
+        with torch.cuda.stream(cstream):
+            bufs[b][0].copy_(pts_h, non_blocking=True)
+            bufs[b][1].copy_(covs_h, non_blocking=True)
+        copied[b].record(cstream)
 
-    e2e_step()
+    def e2e_run(steps, start_event=None):
+        for b in (0, 1):
+            freed[b].record(stream)
+        if start_event is not None:
+            cstream.wait_event(start_event)
+        upload(0)
+        for k in range(steps):
+            b = k % 2
+            stream.wait_event(copied[b])
+            if k + 1 < steps:
+                upload(1 - b)
+            api.rebuild_voxelmaps(maps, bufs[b][0], bufs[b][1])
+            freed[b].record(stream)
+            plan.execute(w.poses, out=out, inliers=inl)
+            out_h.copy_(out, non_blocking=True)
+            inl_h.copy_(inl, non_blocking=True)
+
+    e2e_run(2)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(world)
     e0.record(stream)
-    for _ in range(E):
-        e2e_step()
+    e2e_run(E, start_event=e0)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / E, world, dev)
@@ -459,7 +482,9 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pts,
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"},
             "e2e": {"value": e2e_value, "unit": "source pts/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "pipelining": "upload of step k+1 (copy stream, second buffer) overlaps "
+                                  "step k"},
             "batched_vs_per_factor": comparison,
             "gpu_launches": int(launches),
             "clocks": clk,
