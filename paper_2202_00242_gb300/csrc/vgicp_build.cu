@@ -312,6 +312,7 @@ __device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
 // shared memory (ties by voxel id); vrank[v] = position of voxel v in that order
 // and vorder[rank] = v.
 constexpr int kSortThreads = 1024;
+constexpr int kSortReg = 16;  // elements per thread in the register stages
 __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
     const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank,
@@ -335,8 +336,38 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
   for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
     sk[i] = i < cnt ? (((unsigned long long)morton_of_key(vkeys[first + i]) << 32) | i) : ~0ull;
   __syncthreads();
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+  // bitonic network; the stages of stride < kSortReg run in registers on blocks
+  // of kSortReg consecutive elements (one block per thread), the others in
+  // shared memory
+  const bool reg = N >= (uint32_t)kSortReg;
+  const uint32_t b0 = threadIdx.x * kSortReg;
+  const bool owner = reg && b0 < N;
+  if (owner) {  // k = 2 .. kSortReg entirely inside the block
+    unsigned long long r[kSortReg];
+#pragma unroll
+    for (int e = 0; e < kSortReg; ++e) r[e] = sk[b0 + e];
+#pragma unroll
+    for (int k = 2; k <= kSortReg; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int e = 0; e < kSortReg; ++e) {
+          const int q = e ^ j;
+          if (q > e) {
+            const bool up = (((b0 + e) & k) == 0);
+            const unsigned long long a = r[e], b = r[q];
+            if ((a > b) == up) {
+              r[e] = b;
+              r[q] = a;
+            }
+          }
+        }
+#pragma unroll
+    for (int e = 0; e < kSortReg; ++e) sk[b0 + e] = r[e];
+  }
+  __syncthreads();
+  for (uint32_t k = reg ? 2 * kSortReg : 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0 && (!reg || j >= (uint32_t)kSortReg); j >>= 1) {
       for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
         const uint32_t q = i ^ j;
         if (q > i) {
@@ -350,6 +381,28 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
       }
       __syncthreads();
     }
+    if (owner) {  // strides kSortReg / 2 .. 1: direction fixed over the block
+      const bool up = (b0 & k) == 0;
+      unsigned long long r[kSortReg];
+#pragma unroll
+      for (int e = 0; e < kSortReg; ++e) r[e] = sk[b0 + e];
+#pragma unroll
+      for (int j = kSortReg >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int e = 0; e < kSortReg; ++e) {
+          const int q = e ^ j;
+          if (q > e) {
+            const unsigned long long a = r[e], b = r[q];
+            if ((a > b) == up) {
+              r[e] = b;
+              r[q] = a;
+            }
+          }
+        }
+#pragma unroll
+      for (int e = 0; e < kSortReg; ++e) sk[b0 + e] = r[e];
+    }
+    if (reg) __syncthreads();
   }
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const uint32_t v = first + (uint32_t)(sk[i] & 0xFFFFFFFFull);
