@@ -98,13 +98,9 @@ __global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
     uint32_t h = hash_key(kx, ky, kz) & mask;
     uint32_t found = kNoSlot;
     for (int p = 0; p < max_probe; ++p) {
-      Slot* s = slots + base + h;
-      unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&s->key);
-      if (cur == kEmptyKey) {
-        cur = atomicCAS(&s->key, kEmptyKey, key);
-        if (cur == kEmptyKey) cur = key;
-      }
-      if (cur == key) {
+      // one round trip: the CAS either claims an empty slot or returns its key
+      const unsigned long long cur = atomicCAS(&slots[base + h].key, kEmptyKey, key);
+      if (cur == kEmptyKey || cur == key) {
         found = (uint32_t)(base + h);
         break;
       }
@@ -161,16 +157,26 @@ __global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __r
   vbase[m] = (o < n_total) ? vid[o] : *n_vox;
 }
 
+// Per voxel: the base of its point list (the grouped offset of its rank), in
+// voxel order, so that the scatter needs one indirection less.
+__global__ void list_base_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
+                                 const uint32_t* __restrict__ vrank,
+                                 const uint32_t* __restrict__ goff, uint32_t* __restrict__ base) {
+  const int64_t V = *n_vox;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
+       v += (int64_t)gridDim.x * blockDim.x)
+    base[v] = goff[vrank[v]];
+}
+
 __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot,
-                               const Slot* __restrict__ slots, const uint32_t* __restrict__ vrank,
-                               const uint32_t* __restrict__ goff, uint32_t* vfill,
-                               uint32_t* __restrict__ plist) {
+                               const Slot* __restrict__ slots, const uint32_t* __restrict__ base,
+                               uint32_t* vfill, uint32_t* __restrict__ plist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = pt_slot[i];
     if (s == kNoSlot) continue;
     const uint32_t v = slots[s].vid;
-    const uint32_t pos = goff[vrank[v]] + atomicAdd(vfill + v, 1u);
+    const uint32_t pos = base[v] + atomicAdd(vfill + v, 1u);
     plist[pos] = (uint32_t)i;
   }
 }
@@ -716,9 +722,11 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp,
                              s->d_num_valid, st);
   if (rc != VGICP_OK) return rc;
+  list_base_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_goff,
+                                            s->d_vslot_of);
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
-  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, vrank, s->d_goff,
-                                         s->d_vfill, s->d_plist);
+  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of, s->d_vfill,
+                                         s->d_plist);
   finalize_kernel<<<g, kFinThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
                                              vorder, s->d_goff, s->d_plist, s->d_recs,
                                              s->d_gpts, s->d_gcovs);
@@ -732,9 +740,9 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
                                               s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
                                               s->max_probe, s->d_vslots, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, first, assign, vbase, scatter, sort, rank counts, finalize, vslot init/insert
-  // (+ init: 1)
-  count_launches(10);
+  // insert, first, assign, vbase, sort, rank counts, list bases, scatter, finalize,
+  // vslot init/insert (+ init: 1)
+  count_launches(11);
   return VGICP_OK;
 }
 

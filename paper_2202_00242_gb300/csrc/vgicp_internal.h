@@ -58,6 +58,7 @@ struct MapSet {
   uint32_t* d_voff = nullptr;     // n_total: voxel at each rank
   uint32_t* d_vfill = nullptr;    // n_total: first-point flags, counts by rank, list fill
   uint32_t* d_plist = nullptr;    // n_total: point lists of the voxels, in rank order
+  uint32_t* d_vslot_of = nullptr; // n_total: list base of each voxel
   float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
   float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
   uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
