@@ -86,9 +86,9 @@ typedef struct {
 /* Build the voxel map of one target cloud.  points: n x 3, covs: n x 6 (device,
  * read during the call's kernels only).  resolution > 0.  n >= 0 (an empty map
  * is valid).  *out receives a new handle.  The call synchronizes the stream once,
- * after counting the voxels, to size the lookup table (capacity next pow2 >= 8 V,
- * 64 B per slot); the rest is asynchronous: check vgicp_voxelmap_status() before
- * relying on the contents. */
+ * after counting the voxels, to size the lookup table (next pow2 >= max(8 V,
+ * 2 n) slots of 64 B); the rest is asynchronous: check vgicp_voxelmap_status()
+ * before relying on the contents. */
 int vgicp_build_voxelmap(const float* points, const float* covs, int64_t n, double resolution,
                          const vgicp_map_opts* opts, vgicp_stream_t stream, vgicp_map** out);
 
@@ -104,9 +104,9 @@ int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t*
 /* Rebuild maps in place from new clouds of the same sizes.  maps must be all
  * handles of one vgicp_build_voxelmaps() call (or the single handle of
  * vgicp_build_voxelmap()), in their original order.  No allocation and no
- * synchronization: each lookup table keeps the capacity of the first build, so
- * clouds with more voxels run at a higher load factor, and a voxel that does not
- * fit within max_probe slots sets VGICP_ERR_HASH_FULL (build anew then). */
+ * synchronization: each lookup table keeps the region of the first build (at
+ * least 2 n slots), so clouds with more voxels run at a higher load factor,
+ * never above 1/2. */
 int vgicp_rebuild_voxelmaps(vgicp_map* const* maps, int32_t n_maps, const float* points,
                             const float* covs, vgicp_stream_t stream);
 

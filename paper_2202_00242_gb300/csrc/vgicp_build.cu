@@ -625,8 +625,9 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max, cons
 }
 
 // First build of a set: reads the per-map voxel counts back (one stream
-// synchronization) and allocates each map's lookup table at capacity
-// next_pow2(max(16, kLookupLoad V)).
+// synchronization) and allocates each map's lookup-table region at
+// next_pow2(max(16, kLookupLoad V, 2 n)) slots; a build uses
+// min(next_pow2(kLookupLoad V), region) of it.
 int size_lookup_tables(MapSet* s, cudaStream_t st) {
   std::vector<uint32_t> vb((size_t)s->n_maps + 1);
   VGICP_CUDA_TRY(cudaMemcpyAsync(vb.data(), s->d_vbase, sizeof(uint32_t) * vb.size(),
@@ -636,8 +637,12 @@ int size_lookup_tables(MapSet* s, cudaStream_t st) {
   int64_t total = 0;
   for (int32_t m = 0; m < s->n_maps; ++m) {
     const uint64_t V = vb[m + 1] >= vb[m] ? vb[m + 1] - vb[m] : 0;
+    // at least 2 n slots, so that a rebuild with up to V = n voxels still fits
+    // (load factor <= 1/2); the first build's capacity next_pow2(kLookupLoad V)
+    // when larger
+    const uint64_t nm = (uint64_t)(s->point_off[m + 1] - s->point_off[m]);
     uint64_t c = 16;
-    while (c < kLookupLoad * V) c <<= 1;
+    while (c < kLookupLoad * V || c < 2 * nm) c <<= 1;
     s->vslot_base[m] = total;
     total += (int64_t)c;
   }

@@ -376,3 +376,46 @@ def test_factor_candidates_threshold(dev):
             T = api.relative_poses(w.world_poses, [[j, i]])[0]
             o = oracle.overlap(omaps[j], w.clouds.cloud(i)[0], T)
             assert ((j, i) in got) == (o >= 0.05), (j, i, o)
+
+
+def test_plan_27_neighbours_matches_oracle(dev):
+    """A 27-neighbour factor set as a plan (CUDA graph, autotuned item size)."""
+    w = cases.workload_with_knn_covs("outdoor", seed=35, n_submaps=6, neighbours=2)
+    w_r = 0.5
+    pts, covs = cu(w.clouds.points), cu(w.clouds.covs)
+    maps = api.build_voxelmaps(pts, covs, w.clouds.offsets, w_r)
+    maps[0].status()
+    plan = api.Plan(maps, maps, w.pairs, neighbours=27)
+    plan.autotune(w.poses)
+    res = plan.execute(w.poses)
+    for p, (j, i) in enumerate(w.pairs[:4]):
+        ref = oracle.linearize(oracle.build_voxelmap(*w.clouds.cloud(j), w_r),
+                               *w.clouds.cloud(i), w.poses[p], neighbours=27, nthreads=0)
+        check_factor(res.out[p], res.inliers[p], ref, f"27-neighbour plan pair {p}")
+    plan.close()
+
+
+def test_rebuild_with_more_voxels_keeps_parity(dev):
+    """A rebuild keeps the lookup-table region of the first build (sized from its
+    voxel count, and at least 2 n slots); clouds of the same size with many more
+    voxels still give the oracle's map and factors."""
+    rng = np.random.default_rng(12)
+    n = 6000
+    dense = (rng.normal(size=(n, 3)) * 0.6).astype(np.float32)   # few voxels
+    sparse = (rng.random((n, 3)) * 12.0 - 6.0).astype(np.float32)  # many more
+    covs = np.tile(np.array([0.02, 0, 0, 0.02, 0, 0.02], np.float32), (n, 1))
+    r = 0.5
+    vm = api.VoxelMap.build(cu(dense), cu(covs), r)
+    vm.status()
+    v_first = vm.info()[0]
+    api.rebuild_voxelmaps([vm], cu(sparse), cu(covs))
+    vm.status()
+    ex = vm.export()
+    ref = oracle.build_voxelmap(sparse, covs, r)
+    assert ref.num_voxels > 4 * v_first
+    assert np.array_equal(ex["keys"], ref.keys) and np.array_equal(ex["counts"], ref.counts)
+    src = sparse[::3] + np.float32(0.05)
+    T = np.eye(4)
+    lin = api.linearize(vm, cu(src), cu(covs[::3]), T)
+    refl = oracle.linearize(ref, src, covs[::3], T)
+    check_factor(lin.out, lin.inliers, refl, "after rebuild")
