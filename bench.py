@@ -459,10 +459,14 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         n_done, secs, pairs_done = oracle_sample(w, args.cpu_seconds, cores)
+        n1, secs1, pairs1 = oracle_sample(w, min(3.0, args.cpu_seconds), 1)
         cpu = {"value": n_done / secs, "unit": "source pts/s", "cores": cores, "kind": "oracle",
                "sample": f"first {pairs_done} of {P} pairs in order (their target maps built by "
                          f"the oracle inside the timed sample), {n_done} source points, "
-                         f"{secs:.1f} s, FP64, OpenMP over {cores} threads"}
+                         f"{secs:.1f} s, FP64, OpenMP over {cores} threads",
+               "single_thread": {"value": n1 / secs1, "unit": "source pts/s",
+                                 "sample": f"first {pairs1} pairs, {n1} source points, "
+                                           f"{secs1:.1f} s, one thread"}}
 
     if rank == 0:
         line = {

@@ -84,7 +84,8 @@ typedef struct {
 } vgicp_map_opts;
 
 /* Build the voxel map of one target cloud.  points: n x 3, covs: n x 6 (device,
- * read during the call's kernels only).  resolution > 0.  n >= 0 (an empty map
+ * read during the call's kernels only; symmetric positive semi-definite, as the
+ * regularised k-nearest-neighbour covariances are).  resolution > 0.  n >= 0 (an empty map
  * is valid).  *out receives a new handle.  The call synchronizes the stream once,
  * after counting the voxels, to size the lookup table (next pow2 >= max(8 V,
  * 2 n) slots of 64 B); the rest is asynchronous: check vgicp_voxelmap_status()

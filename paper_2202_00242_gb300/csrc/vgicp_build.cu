@@ -499,12 +499,22 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
     sl.mu[0] = r0.x;
     sl.mu[1] = r0.y;
     sl.mu[2] = r0.z;
-    sl.cov[0] = r1.x;
-    sl.cov[1] = r1.y;
-    sl.cov[2] = r1.z;
-    sl.cov[3] = r1.w;
-    sl.cov[4] = r2.x;
-    sl.cov[5] = r2.y;
+    // the Cholesky factor L of C' (the linearization forms R^T C' R as (R^T L)(R^T L)^T);
+    // a non-positive pivot (a semi-definite C') leaves its column zero
+    const float l00 = r1.x > 0.f ? sqrtf(r1.x) : 0.f;
+    const float il0 = l00 > 0.f ? 1.0f / l00 : 0.f;
+    const float l10 = r1.y * il0, l20 = r1.z * il0;
+    const float p11 = r1.w - l10 * l10;
+    const float l11 = p11 > 0.f ? sqrtf(p11) : 0.f;
+    const float l21 = l11 > 0.f ? (r2.x - l20 * l10) / l11 : 0.f;
+    const float p22 = r2.y - l20 * l20 - l21 * l21;
+    const float l22 = p22 > 0.f ? sqrtf(p22) : 0.f;
+    sl.cov[0] = l00;
+    sl.cov[1] = l10;
+    sl.cov[2] = l20;
+    sl.cov[3] = l11;
+    sl.cov[4] = l21;
+    sl.cov[5] = l22;
     sl.pad1[0] = 0.0f;
     sl.pad1[1] = 0.0f;
   }

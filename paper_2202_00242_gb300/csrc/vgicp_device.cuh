@@ -37,7 +37,8 @@ constexpr int kRecordF4 = 3;
 // Lookup table slot with the voxel Gaussian inline (64 B, 64-B aligned): one
 // probe is two independent 256-bit loads.
 //   bytes  0..31: key (u64), vid (u32), count (u32), mu' (3 x f32), spill (u32)
-//   bytes 32..63: C' (6 x f32, xx xy xz yy yz zz), pad
+//   bytes 32..63: L, the Cholesky factor of C' (6 x f32: l00 l10 l20 l11 l21
+//                 l22), pad
 // Linear probing from the key's home slot h.  spill (of slot h) is nonzero iff
 // some key whose home is h lies further along the probe sequence, so a lookup
 // whose home slot holds another key and has spill == 0 is a miss after one

@@ -10,7 +10,9 @@
 //   vid  = hash lookup (open addressing, bounded linear probe)
 //   in the SOURCE frame (J = R K with K = [[mu]x, -I], so J^T W J = K^T W' K):
 //   d'   = R^T (mu'_v - q)
-//   M'   = R^T C'_v R + C_k,  W' = M'^-1  (= R^T W R, symmetric adjugate / det)
+//   M'   = R^T C'_v R + C_k = B B^T + C_k with B = R^T L (C'_v = L L^T, the
+//          Cholesky factor kept in the lookup slot), W' = M'^-1 (= R^T W R,
+//          symmetric adjugate / det)
 //   u    = W' d'
 //   err += d'^T u
 //   b   += [ u x mu ; -u ]
@@ -160,6 +162,30 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// M' = R^T C' R + C (upper triangle m00 m01 m02 m11 m12 m22) from the voxel
+// covariance's Cholesky factor L (C' = L L^T, stored in the lookup slot as
+// l00 l10 l20 l11 l21 l22): with B = R^T L, R^T C' R = B B^T (36 operations
+// instead of 45 for R^T (C' R)).
+__device__ __forceinline__ void fused_cov(const float* R, const float4 r1, const float4 r2,
+                                          const float* c, float& m00, float& m01, float& m02,
+                                          float& m11, float& m12, float& m22) {
+  const float l00 = r1.x, l10 = r1.y, l20 = r1.z, l11 = r1.w, l21 = r2.x, l22 = r2.y;
+  // B_i0 = sum_k R_ki L_k0, B_i1 = R_1i l11 + R_2i l21, B_i2 = R_2i l22
+  const float b00 = fmaf(R[0], l00, fmaf(R[3], l10, R[6] * l20));
+  const float b10 = fmaf(R[1], l00, fmaf(R[4], l10, R[7] * l20));
+  const float b20 = fmaf(R[2], l00, fmaf(R[5], l10, R[8] * l20));
+  const float b01 = fmaf(R[3], l11, R[6] * l21);
+  const float b11 = fmaf(R[4], l11, R[7] * l21);
+  const float b21 = fmaf(R[5], l11, R[8] * l21);
+  const float b02 = R[6] * l22, b12 = R[7] * l22, b22 = R[8] * l22;
+  m00 = fmaf(b00, b00, fmaf(b01, b01, fmaf(b02, b02, c[0])));
+  m01 = fmaf(b00, b10, fmaf(b01, b11, fmaf(b02, b12, c[1])));
+  m02 = fmaf(b00, b20, fmaf(b01, b21, fmaf(b02, b22, c[2])));
+  m11 = fmaf(b10, b10, fmaf(b11, b11, fmaf(b12, b12, c[3])));
+  m12 = fmaf(b10, b20, fmaf(b11, b21, fmaf(b12, b22, c[4])));
+  m22 = fmaf(b20, b20, fmaf(b21, b21, fmaf(b22, b22, c[5])));
+}
+
 __device__ __forceinline__ void add_term_t(float* acc, const float* R, float x, float y, float z,
                                            const float* c, float tx, float ty, float tz,
                                            const float4 r1, const float4 r2) {
@@ -167,25 +193,9 @@ __device__ __forceinline__ void add_term_t(float* acc, const float* R, float x, 
   const float d0 = fmaf(R[0], tx, fmaf(R[3], ty, R[6] * tz));
   const float d1 = fmaf(R[1], tx, fmaf(R[4], ty, R[7] * tz));
   const float d2 = fmaf(R[2], tx, fmaf(R[5], ty, R[8] * tz));
-  // voxel covariance C' (symmetric)
-  const float v00 = r1.x, v01 = r1.y, v02 = r1.z, v11 = r1.w, v12 = r2.x, v22 = r2.y;
-  // A = C' R
-  const float a00 = fmaf(v00, R[0], fmaf(v01, R[3], v02 * R[6]));
-  const float a01 = fmaf(v00, R[1], fmaf(v01, R[4], v02 * R[7]));
-  const float a02 = fmaf(v00, R[2], fmaf(v01, R[5], v02 * R[8]));
-  const float a10 = fmaf(v01, R[0], fmaf(v11, R[3], v12 * R[6]));
-  const float a11 = fmaf(v01, R[1], fmaf(v11, R[4], v12 * R[7]));
-  const float a12 = fmaf(v01, R[2], fmaf(v11, R[5], v12 * R[8]));
-  const float a20 = fmaf(v02, R[0], fmaf(v12, R[3], v22 * R[6]));
-  const float a21 = fmaf(v02, R[1], fmaf(v12, R[4], v22 * R[7]));
-  const float a22 = fmaf(v02, R[2], fmaf(v12, R[5], v22 * R[8]));
-  // M' = R^T A + C_k (upper triangle)
-  const float m00 = fmaf(R[0], a00, fmaf(R[3], a10, fmaf(R[6], a20, c[0])));
-  const float m01 = fmaf(R[0], a01, fmaf(R[3], a11, fmaf(R[6], a21, c[1])));
-  const float m02 = fmaf(R[0], a02, fmaf(R[3], a12, fmaf(R[6], a22, c[2])));
-  const float m11 = fmaf(R[1], a01, fmaf(R[4], a11, fmaf(R[7], a21, c[3])));
-  const float m12 = fmaf(R[1], a02, fmaf(R[4], a12, fmaf(R[7], a22, c[4])));
-  const float m22 = fmaf(R[2], a02, fmaf(R[5], a12, fmaf(R[8], a22, c[5])));
+  // M' = R^T C' R + C_k (upper triangle)
+  float m00, m01, m02, m11, m12, m22;
+  fused_cov(R, r1, r2, c, m00, m01, m02, m11, m12, m22);
   // W' = adj(M') / det(M')
   const float i00 = fmaf(m11, m22, -m12 * m12);
   const float i01 = fmaf(m02, m12, -m01 * m22);
@@ -660,22 +670,8 @@ __device__ __forceinline__ void eval_term(float* acc, const Pose32& P, float x, 
   const float d0 = fmaf(R[0], tx, fmaf(R[3], ty, R[6] * tz));
   const float d1 = fmaf(R[1], tx, fmaf(R[4], ty, R[7] * tz));
   const float d2 = fmaf(R[2], tx, fmaf(R[5], ty, R[8] * tz));
-  const float v00 = r1.x, v01 = r1.y, v02 = r1.z, v11 = r1.w, v12 = r2.x, v22 = r2.y;
-  const float a00 = fmaf(v00, R[0], fmaf(v01, R[3], v02 * R[6]));
-  const float a01 = fmaf(v00, R[1], fmaf(v01, R[4], v02 * R[7]));
-  const float a02 = fmaf(v00, R[2], fmaf(v01, R[5], v02 * R[8]));
-  const float a10 = fmaf(v01, R[0], fmaf(v11, R[3], v12 * R[6]));
-  const float a11 = fmaf(v01, R[1], fmaf(v11, R[4], v12 * R[7]));
-  const float a12 = fmaf(v01, R[2], fmaf(v11, R[5], v12 * R[8]));
-  const float a20 = fmaf(v02, R[0], fmaf(v12, R[3], v22 * R[6]));
-  const float a21 = fmaf(v02, R[1], fmaf(v12, R[4], v22 * R[7]));
-  const float a22 = fmaf(v02, R[2], fmaf(v12, R[5], v22 * R[8]));
-  const float m00 = fmaf(R[0], a00, fmaf(R[3], a10, fmaf(R[6], a20, c[0])));
-  const float m01 = fmaf(R[0], a01, fmaf(R[3], a11, fmaf(R[6], a21, c[1])));
-  const float m02 = fmaf(R[0], a02, fmaf(R[3], a12, fmaf(R[6], a22, c[2])));
-  const float m11 = fmaf(R[1], a01, fmaf(R[4], a11, fmaf(R[7], a21, c[3])));
-  const float m12 = fmaf(R[1], a02, fmaf(R[4], a12, fmaf(R[7], a22, c[4])));
-  const float m22 = fmaf(R[2], a02, fmaf(R[5], a12, fmaf(R[8], a22, c[5])));
+  float m00, m01, m02, m11, m12, m22;
+  fused_cov(R, r1, r2, c, m00, m01, m02, m11, m12, m22);
   const float i00 = fmaf(m11, m22, -m12 * m12);
   const float i01 = fmaf(m02, m12, -m01 * m22);
   const float i02 = fmaf(m01, m12, -m02 * m11);
