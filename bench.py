@@ -641,9 +641,11 @@ def run_workload(args):
                                                                    else 2000))
         budget = 24 << 30
         state = {}
+        pts_h = torch.from_numpy(w.clouds.points).pin_memory()  # the clouds stay on the host
+        covs_h = torch.from_numpy(w.clouds.covs).pin_memory()
 
         def step():
-            state["r"] = api.linearize_admitted(w.clouds.points, w.clouds.covs, w.clouds.offsets,
+            state["r"] = api.linearize_admitted(pts_h, covs_h, w.clouds.offsets,
                                                 w.pairs, w.poses, w.resolution, budget=budget,
                                                 neighbours=27)
         n_pts = int(w.source_points_per_step)
@@ -652,7 +654,7 @@ def run_workload(args):
         extra["step"] = ("admission batches under a 24 GB budget: per batch, upload the "
                          "submaps from host memory, build their maps, one batched "
                          "27-neighbour linearization")
-        extra["inputs"] = "host memory (7.2 GB of clouds, uploaded inside every step)"
+        extra["inputs"] = "pinned host memory (7.2 GB of clouds, uploaded inside every step)"
     launches0 = lib.vgicp_launch_count()
     clocks = ClockSampler(gpu_uuid(torch))
     clocks.start()

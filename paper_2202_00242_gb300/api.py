@@ -561,12 +561,18 @@ def admission_schedule(map_bytes, pairs, budget, src_bytes=None):
     return out, nb.value
 
 
+def _host_rows(x, a, b):
+    return x[a:b] if isinstance(x, torch.Tensor) else torch.from_numpy(x[a:b])
+
+
 def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution, budget,
                        neighbours=27, tile=0, stream=None):
     """Linearize factors among submaps that live in host memory, batch by batch:
     each batch's submaps are uploaded, built into voxel maps (which also serve
-    as the sources), linearized in one batched launch, and released.  Returns
-    (out (P, 43) float64 host, inliers (P,) host, n_batches)."""
+    as the sources), linearized in one batched launch, and released.
+    ``points_host`` / ``covs_host``: numpy arrays or CPU tensors (pinned tensors
+    upload at full speed).  Returns (out (P, 43) float64 host, inliers (P,) host,
+    n_batches)."""
     off = np.asarray(offsets, dtype=np.int64)
     pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     P = pairs.shape[0]
@@ -584,9 +590,9 @@ def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution
         pts = torch.empty((int(boff[-1]), 3), dtype=torch.float32, device=dev)
         cvs = torch.empty((int(boff[-1]), 6), dtype=torch.float32, device=dev)
         for k, m in enumerate(used):
-            pts[boff[k]:boff[k + 1]].copy_(torch.from_numpy(points_host[off[m]:off[m + 1]]),
+            pts[boff[k]:boff[k + 1]].copy_(_host_rows(points_host, off[m], off[m + 1]),
                                            non_blocking=True)
-            cvs[boff[k]:boff[k + 1]].copy_(torch.from_numpy(covs_host[off[m]:off[m + 1]]),
+            cvs[boff[k]:boff[k + 1]].copy_(_host_rows(covs_host, off[m], off[m + 1]),
                                            non_blocking=True)
         maps = build_voxelmaps(pts, cvs, boff, resolution, stream=stream)
         maps[0].status()
