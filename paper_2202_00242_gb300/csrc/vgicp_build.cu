@@ -30,6 +30,7 @@
 
 #include "vgicp_device.cuh"
 #include "vgicp_internal.h"
+#include "vgicp_mean.h"
 
 namespace vgicp {
 namespace {
@@ -267,28 +268,42 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
 #pragma unroll
         for (int k = 0; k < 9; ++k) df_add(hi[k], lo[k], f[k], exact);
       }
-      double sum[9];
+      // q = RN32(RN64(sum / N)) per component: from the exact float pair in
+      // float32 where certified, else (rare) from the binary64 definition
+      float q[9];
+      uint32_t need64 = exact ? 0u : 0x1FFu;
       if (exact) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) sum[k] = __dadd_rn((double)hi[k], (double)lo[k]);  // exact
-      } else {
-        // binary64 sum in ascending point index (the grouped order; rare: large
-        // dynamic range)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) sum[k] = 0.0;
-        for (uint32_t a = 0; a < c; ++a) {
-          const int64_t d = (int64_t)o + a;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) sum[k] = __dadd_rn(sum[k], (double)gpts[3 * d + k]);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) sum[3 + k] = __dadd_rn(sum[3 + k], (double)gcovs[6 * d + k]);
+        for (int k = 0; k < 9; ++k) {
+          bool ok;
+          q[k] = mean_rn32(hi[k], lo[k], c, ok);
+          if (!ok) need64 |= 1u << k;
         }
       }
-      const double N = (double)c;
-      const double y = __drcp_rn(N);
-      float q[9];
+      if (need64) {
+        double sum[9];
+        if (exact) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) q[k] = __double2float_rn(div_rn(sum[k], N, y));
+          for (int k = 0; k < 9; ++k) sum[k] = __dadd_rn((double)hi[k], (double)lo[k]);  // exact
+        } else {
+          // binary64 sum in ascending point index (the grouped order; rare: large
+          // dynamic range)
+#pragma unroll
+          for (int k = 0; k < 9; ++k) sum[k] = 0.0;
+          for (uint32_t a = 0; a < c; ++a) {
+            const int64_t d = (int64_t)o + a;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sum[k] = __dadd_rn(sum[k], (double)gpts[3 * d + k]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sum[3 + k] = __dadd_rn(sum[3 + k], (double)gcovs[6 * d + k]);
+          }
+        }
+        const double N = (double)c;
+        const double y = __drcp_rn(N);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (need64 & (1u << k)) q[k] = __double2float_rn(div_rn(sum[k], N, y));
+      }
       recs[3 * v + 0] = make_float4(q[0], q[1], q[2], __uint_as_float(c));
       recs[3 * v + 1] = make_float4(q[3], q[4], q[5], q[6]);
       recs[3 * v + 2] = make_float4(q[7], q[8], 0.0f, 0.0f);
@@ -317,8 +332,48 @@ __device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
 // One CTA per (map, chunk): bitonic sort of the chunk's voxels by Morton code in
 // shared memory (ties by voxel id); vrank[v] = position of voxel v in that order
 // and vorder[rank] = v.
+//
+// Element i lives at i + i / 16 (one pad word per 16), which keeps every access
+// pattern below free of bank conflicts.  Each pass loads a group of up to 16
+// elements per thread into registers and applies up to four consecutive stages
+// of the network there: a group is the elements i0 + t s (t < 2^M), closed under
+// the strides s .. s 2^(M-1), so a merge level of stride 2^(p-1) .. 1 takes
+// ceil(p / 4) passes through shared memory instead of p.
 constexpr int kSortThreads = 1024;
-constexpr int kSortReg = 16;  // elements per thread in the register stages
+constexpr int kSortSmemElems = kMortonChunk + kMortonChunk / 16;
+
+__device__ __forceinline__ uint32_t sort_phys(uint32_t i) { return i + (i >> 4); }
+
+__device__ __forceinline__ void cmp_swap(unsigned long long& a, unsigned long long& b, bool up) {
+  if ((a > b) == up) {
+    const unsigned long long t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// The stages of strides s 2^(M-1) .. s of merge level k on every group.
+template <int M>
+__device__ __forceinline__ void bitonic_pass(unsigned long long* sk, uint32_t N, uint32_t k,
+                                             uint32_t s_log) {
+  constexpr int G = 1 << M;
+  const uint32_t s = 1u << s_log;
+  for (uint32_t g = threadIdx.x; g < (N >> M); g += blockDim.x) {
+    const uint32_t i0 = ((g >> s_log) << (s_log + M)) | (g & (s - 1u));
+    const bool up = (i0 & k) == 0u;  // the same for the whole group (its bits are below k)
+    unsigned long long r[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) r[t] = sk[sort_phys(i0 + (uint32_t)t * s)];
+#pragma unroll
+    for (int j = G >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int t = 0; t < G; ++t)
+        if ((t ^ j) > t) cmp_swap(r[t], r[t ^ j], up);
+#pragma unroll
+    for (int t = 0; t < G; ++t) sk[sort_phys(i0 + (uint32_t)t * s)] = r[t];
+  }
+}
+
 __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
     const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank,
@@ -336,82 +391,50 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
   }
   return;
 #endif
-  uint32_t N = 1;
+  uint32_t N = 16;  // at least one full register group
   while (N < cnt) N <<= 1;
   const uint32_t first = vbase[m] + lo;
   for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
-    sk[i] = i < cnt ? (((unsigned long long)morton_of_key(vkeys[first + i]) << 32) | i) : ~0ull;
+    sk[sort_phys(i)] =
+        i < cnt ? (((unsigned long long)morton_of_key(vkeys[first + i]) << 32) | i) : ~0ull;
   __syncthreads();
-  // bitonic network; the stages of stride < kSortReg run in registers on blocks
-  // of kSortReg consecutive elements (one block per thread), the others in
-  // shared memory
-  const bool reg = N >= (uint32_t)kSortReg;
-  const uint32_t b0 = threadIdx.x * kSortReg;
-  const bool owner = reg && b0 < N;
-  if (owner) {  // k = 2 .. kSortReg entirely inside the block
-    unsigned long long r[kSortReg];
+  // levels k = 2 .. 16: inside blocks of 16 consecutive elements
+  for (uint32_t g = threadIdx.x; g < (N >> 4); g += blockDim.x) {
+    unsigned long long r[16];
 #pragma unroll
-    for (int e = 0; e < kSortReg; ++e) r[e] = sk[b0 + e];
+    for (int t = 0; t < 16; ++t) r[t] = sk[sort_phys(16u * g + t)];
 #pragma unroll
-    for (int k = 2; k <= kSortReg; k <<= 1)
+    for (int k = 2; k <= 16; k <<= 1)
 #pragma unroll
       for (int j = k >> 1; j > 0; j >>= 1)
 #pragma unroll
-        for (int e = 0; e < kSortReg; ++e) {
-          const int q = e ^ j;
-          if (q > e) {
-            const bool up = (((b0 + e) & k) == 0);
-            const unsigned long long a = r[e], b = r[q];
-            if ((a > b) == up) {
-              r[e] = b;
-              r[q] = a;
-            }
-          }
-        }
+        for (int t = 0; t < 16; ++t)
+          if ((t ^ j) > t) cmp_swap(r[t], r[t ^ j], ((16u * g + t) & (uint32_t)k) == 0u);
 #pragma unroll
-    for (int e = 0; e < kSortReg; ++e) sk[b0 + e] = r[e];
+    for (int t = 0; t < 16; ++t) sk[sort_phys(16u * g + t)] = r[t];
   }
   __syncthreads();
-  for (uint32_t k = reg ? 2 * kSortReg : 2; k <= N; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0 && (!reg || j >= (uint32_t)kSortReg); j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint32_t q = i ^ j;
-        if (q > i) {
-          const unsigned long long a = sk[i], b = sk[q];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            sk[i] = b;
-            sk[q] = a;
-          }
-        }
-      }
+  // levels k = 32 .. N: strides 2^(p-1) .. 1 in passes of up to four, the
+  // partial pass (p mod 4 strides) first
+  for (uint32_t p = 5; (1u << p) <= N; ++p) {
+    const uint32_t k = 1u << p;
+    int top = (int)p - 1;  // log2 of the largest stride not yet applied
+    const int rem = (int)(p & 3u);
+    if (rem) {
+      const uint32_t s_log = (uint32_t)(top - rem + 1);
+      if (rem == 1) bitonic_pass<1>(sk, N, k, s_log);
+      else if (rem == 2) bitonic_pass<2>(sk, N, k, s_log);
+      else bitonic_pass<3>(sk, N, k, s_log);
+      top -= rem;
       __syncthreads();
     }
-    if (owner) {  // strides kSortReg / 2 .. 1: direction fixed over the block
-      const bool up = (b0 & k) == 0;
-      unsigned long long r[kSortReg];
-#pragma unroll
-      for (int e = 0; e < kSortReg; ++e) r[e] = sk[b0 + e];
-#pragma unroll
-      for (int j = kSortReg >> 1; j > 0; j >>= 1)
-#pragma unroll
-        for (int e = 0; e < kSortReg; ++e) {
-          const int q = e ^ j;
-          if (q > e) {
-            const unsigned long long a = r[e], b = r[q];
-            if ((a > b) == up) {
-              r[e] = b;
-              r[q] = a;
-            }
-          }
-        }
-#pragma unroll
-      for (int e = 0; e < kSortReg; ++e) sk[b0 + e] = r[e];
+    for (; top >= 0; top -= 4) {
+      bitonic_pass<4>(sk, N, k, (uint32_t)(top - 3));
+      __syncthreads();
     }
-    if (reg) __syncthreads();
   }
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const uint32_t v = first + (uint32_t)(sk[i] & 0xFFFFFFFFull);
+    const uint32_t v = first + (uint32_t)(sk[sort_phys(i)] & 0xFFFFFFFFull);
     vrank[v] = first + i;
     vorder[first + i] = v;
   }
@@ -725,10 +748,11 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   if (!sort_attr) {
     VGICP_CUDA_TRY(cudaFuncSetAttribute(morton_sort_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(unsigned long long) * kMortonChunk)));
+                                        (int)(sizeof(unsigned long long) * kSortSmemElems)));
     sort_attr = true;
   }
-  morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kMortonChunk, st>>>(
+  morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kSortSmemElems,
+                       st>>>(
       s->d_chunks, s->d_vbase, s->d_vkeys, vrank, vorder);
   // light kernels over voxels (V <= n is on the device): grid-stride, capped grid
   const int gv = std::min<int>(g, device_sm_count() * 8);
