@@ -137,15 +137,41 @@ __global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_
 __global__ void assign_kernel(int64_t n_total, const uint32_t* __restrict__ first,
                               const uint32_t* __restrict__ vid, const uint32_t* __restrict__ pt_slot,
                               Slot* slots, uint32_t* __restrict__ vcount,
-                              unsigned long long* __restrict__ vkeys) {
+                              unsigned long long* __restrict__ vkeys,
+                              uint32_t* __restrict__ hslot_of) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!first[i]) continue;
     const uint32_t v = vid[i];
-    Slot* s = slots + pt_slot[i];
+    const uint32_t hs = pt_slot[i];
+    Slot* s = slots + hs;
     vcount[v] = s->count;
     vkeys[v] = s->key;
     s->vid = v;
+    hslot_of[v] = hs;
+  }
+}
+
+// Rebuild: empty the build-table and lookup-table slots the previous build's
+// voxels occupy (every slot a build claims belongs to one of its voxels, and
+// spill flags are set only on claimed slots), which leaves both tables empty.
+__global__ void reset_tables_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
+                                    const uint32_t* __restrict__ hslot_of,
+                                    const uint32_t* __restrict__ lslot_of, Slot* slots,
+                                    VSlot* vslots) {
+  const int64_t V = *n_vox;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    Slot e;
+    e.key = kEmptyKey;
+    e.vid = 0xFFFFFFFFu;
+    e.count = 0u;
+    slots[hslot_of[v]] = e;
+    const uint32_t ls = lslot_of[v];
+    if (ls != kNoSlot)
+      asm volatile("st.global.v8.b32 [%0], {%1, %1, %2, %2, %2, %2, %2, %2};" ::"l"(vslots + ls),
+                   "r"(0xFFFFFFFFu), "r"(0u)
+                   : "memory");
   }
 }
 
@@ -182,7 +208,7 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
   }
 }
 
-// Per-voxel sums and the grouped cloud.  A CTA takes 256 consecutive ranks,
+// Per-voxel sums and the grouped cloud.  A CTA takes 128 consecutive ranks,
 // whose point lists are one contiguous segment of plist:
 //   1. the segment is loaded into shared memory (coalesced) and each thread
 //      sorts its voxel's short list there by point index (segments longer than
@@ -192,8 +218,8 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
 //      writes; the random reads all in flight at once);
 //   3. voxel-parallel: each thread sums its voxel's points from the grouped copy
 //      just written (L2-resident) and writes the voxel record.
-constexpr int kFinThreads = 256;
-constexpr int kFinStage = 6144;  // indices staged per CTA
+constexpr int kFinThreads = 128;
+constexpr int kFinStage = 3072;  // indices staged per CTA
 
 __device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
   for (uint32_t a = 1; a < c; ++a) {
@@ -273,10 +299,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
       float q[9];
       uint32_t need64 = exact ? 0u : 0x1FFu;
       if (exact) {
+        const float rN = __frcp_rn((float)c);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
           bool ok;
-          q[k] = mean_rn32(hi[k], lo[k], c, ok);
+          q[k] = mean_rn32(hi[k], lo[k], c, rN, ok);
           if (!ok) need64 |= 1u << k;
         }
       }
@@ -457,22 +484,26 @@ __device__ __forceinline__ uint32_t lookup_capacity(uint32_t nvox) {
   return c;
 }
 
-// Per map (blockIdx.y): lookup-table capacity from its voxel count, empty keys.
+// Per map (blockIdx.y): lookup-table capacity from its voxel count; with
+// clear_all, every slot of the map's region emptied (the first build, whose
+// region is fresh; later builds find the region empty after the reset).
 __global__ void vslot_init_kernel(const int64_t* __restrict__ slot_base,
                                   const uint32_t* __restrict__ vbase, VSlot* vslots,
-                                  uint32_t* __restrict__ vmask) {
+                                  uint32_t* __restrict__ vmask, int32_t clear_all) {
   const int m = blockIdx.y;
   // the region was sized by the first build; a rebuild with more voxels runs at a
   // higher load factor (an insertion past max_probe reports VGICP_ERR_HASH_FULL)
   const uint32_t region = (uint32_t)(slot_base[m + 1] - slot_base[m]);
   const uint32_t cap = min(lookup_capacity(vbase[m + 1] - vbase[m]), region);
-  VSlot* t = vslots + slot_base[m];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
-  {
-    // the whole first 32-B sector (key = empty, spill = 0): no read-modify-write
-    asm volatile("st.global.v8.b32 [%0], {%1, %1, %2, %2, %2, %2, %2, %2};" ::"l"(t + i),
-                 "r"(0xFFFFFFFFu), "r"(0u)
-                 : "memory");
+  if (clear_all) {
+    VSlot* t = vslots + slot_base[m];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < region;
+         i += gridDim.x * blockDim.x) {
+      // the whole first 32-B sector (key = empty, spill = 0): no read-modify-write
+      asm volatile("st.global.v8.b32 [%0], {%1, %1, %2, %2, %2, %2, %2, %2};" ::"l"(t + i),
+                   "r"(0xFFFFFFFFu), "r"(0u)
+                   : "memory");
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) vmask[m] = cap - 1u;
 }
@@ -484,7 +515,8 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
                                     const uint32_t* __restrict__ vmask,
                                     const unsigned long long* __restrict__ vkeys,
                                     const float4* __restrict__ recs, int32_t max_probe,
-                                    VSlot* vslots, int32_t* status) {
+                                    VSlot* vslots, uint32_t* __restrict__ lslot_of,
+                                    int32_t* status) {
   const int64_t V = *n_vox;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
        v += (int64_t)gridDim.x * blockDim.x) {
@@ -511,6 +543,7 @@ __global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ 
       h = (h + 1) & mask;
     }
     if (placed && h != home) atomicOr(&t[home].spill, 1u);
+    lslot_of[v] = placed ? (uint32_t)(slot_base[lo] + h) : kNoSlot;
     if (!placed) {
       set_status(status, VGICP_ERR_HASH_FULL);
       continue;
@@ -699,12 +732,23 @@ int size_lookup_tables(MapSet* s, cudaStream_t st) {
 
 int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t st) {
   const int64_t n = s->n_total;
-  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_status, 0, sizeof(int32_t), st));
-  if (s->cap_total > 0) {
+  // light kernels over voxels (V <= n is on the device): grid-stride, capped grid
+  const int gv = std::min<int>(grid_for(std::max<int64_t>(n, 1), kThreads), device_sm_count() * 8);
+  // was_built: the tables hold only the previous build's voxels (a build that
+  // stops on an error leaves `built` cleared, so the next one starts over)
+  const bool was_built = s->built;
+  s->built = false;
+  if (was_built) {
+    // empty the slots of the previous build's voxels
+    reset_tables_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, s->d_hslot_of,
+                                                 s->d_lslot_of, s->d_slots, s->d_vslots);
+    count_launches(1);
+  } else if (s->cap_total > 0) {
     init_slots_kernel<<<grid_for(s->cap_total, kThreads), kThreads, 0, st>>>(s->d_slots,
                                                                           s->cap_total);
     count_launches(1);
   }
+  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_status, 0, sizeof(int32_t), st));
   if (n == 0) {
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_num_voxels, 0, sizeof(uint32_t), st));
     VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vbase, 0, sizeof(uint32_t) * (s->n_maps + 1), st));
@@ -713,9 +757,11 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
       if (rc != VGICP_OK) return rc;
     }
     vslot_init_kernel<<<dim3(1, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
-                                                              s->d_vslots, s->d_vmask);
+                                                              s->d_vslots, s->d_vmask,
+                                                              was_built ? 0 : 1);
     VGICP_CUDA_TRY(cudaGetLastError());
     count_launches(1);
+    s->built = true;
     return VGICP_OK;
   }
   const float inv_r = (float)(1.0 / s->resolution);
@@ -729,7 +775,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   int rc = launch_exclusive_scan(first, s->d_flag, n, nullptr, s->d_scan_tmp, s->d_num_voxels, st);
   if (rc != VGICP_OK) return rc;
   assign_kernel<<<g, kThreads, 0, st>>>(n, first, s->d_flag, s->d_pt_slot, s->d_slots,
-                                        s->d_vcount, s->d_vkeys);
+                                        s->d_vcount, s->d_vkeys, s->d_hslot_of);
   vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
                                                             s->d_flag, s->d_num_voxels,
                                                             s->d_vbase);
@@ -754,8 +800,6 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kSortSmemElems,
                        st>>>(
       s->d_chunks, s->d_vbase, s->d_vkeys, vrank, vorder);
-  // light kernels over voxels (V <= n is on the device): grid-stride, capped grid
-  const int gv = std::min<int>(g, device_sm_count() * 8);
   rank_counts_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_vcount, gcount);
   VGICP_CUDA_TRY(cudaGetLastError());
   rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp,
@@ -772,16 +816,21 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
     max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);
-  const unsigned gx = (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
+  // the first build empties the whole lookup region; later ones set the masks only
+  const unsigned gx =
+      was_built ? 1u : (unsigned)std::min<int64_t>(64, (max_cap + kThreads - 1) / kThreads);
   vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
-                                                             s->d_vslots, s->d_vmask);
+                                                             s->d_vslots, s->d_vmask,
+                                                             was_built ? 0 : 1);
   vslot_insert_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, s->n_maps, s->d_vbase,
                                               s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
-                                              s->max_probe, s->d_vslots, s->d_status);
+                                              s->max_probe, s->d_vslots, s->d_lslot_of,
+                                              s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
   // insert, first, assign, vbase, sort, rank counts, list bases, scatter, finalize,
-  // vslot init/insert (+ init: 1)
+  // vslot init/insert (+ reset or init: 1)
   count_launches(11);
+  s->built = true;
   return VGICP_OK;
 }
 

@@ -7,8 +7,8 @@
 // division remains.  On a GPU whose binary64 rate is a small fraction of its
 // float32 rate, it is done here in float32:
 //
-//   q  = candidate float32 quotient of |S| / N (a correctly rounded start,
-//        then one Newton correction);
+//   q  = candidate float32 quotient of |S| / N (|S| RN(1/N), then one Newton
+//        correction);
 //   M+, M- = the midpoints between q and its float32 neighbours;
 //   z+- = |S| - M+- N, evaluated exactly: q N = p + e (FMA split), |hi| - p is
 //        exact (Sterbenz), d - e -+ N u / 2 is a float sum checked to be exact
@@ -72,14 +72,6 @@ VGICP_HD float fma(float a, float b, float c) {
   return ::fmaf(a, b, c);
 #endif
 }
-VGICP_HD float div(float a, float b) {
-#ifdef __CUDA_ARCH__
-  return __fdiv_rn(a, b);
-#else
-  volatile float r = a / b;
-  return r;
-#endif
-}
 VGICP_HD uint32_t bits(float f) {
 #ifdef __CUDA_ARCH__
   return __float_as_uint(f);
@@ -110,9 +102,10 @@ VGICP_HD void two_sum_f(float a, float b, float& s, float& e) {
 
 // Returns RN32(RN64(RN64(hi + lo) / n)) and sets ok, or clears ok (the caller
 // then evaluates that definition in binary64).  Requires hi = RN32(hi + lo)
-// (|lo| <= ulp(hi) / 2), as the exact double-float sums provide.  Certified
-// range: n <= 2^24 and 2^-60 <= |hi| <= 2^100, or hi = lo = 0.
-VGICP_HD float mean_rn32(float hi, float lo, uint32_t n, bool& ok) {
+// (|lo| <= ulp(hi) / 2), as the exact double-float sums provide, and
+// rN = RN32(1 / n) (shared by the components of one voxel).  Certified range:
+// n <= 2^24 and 2^-60 <= |hi| <= 2^100, or hi = lo = 0.
+VGICP_HD float mean_rn32(float hi, float lo, uint32_t n, float rN, bool& ok) {
   using namespace mean32;
   ok = false;
   if (hi == 0.0f) {
@@ -125,13 +118,13 @@ VGICP_HD float mean_rn32(float hi, float lo, uint32_t n, bool& ok) {
   const float l = hi < 0.0f ? -lo : lo;                 // |S| = a + l
   const float N = (float)n;                             // exact
   const float win = mul(a, 0x1p-50f);                   // double-rounding window
-  float q = div(a, N);
-  {  // one Newton step: q + (|S| - q N) / N
+  float q = mul(a, rN);  // within 2 ulp of |S| / N
+  {  // one Newton step: q + (|S| - q N) / N, then within about 1 ulp
     const float p = mul(q, N);
     const float R = add(sub(sub(a, p), fma(q, N, -p)), l);
-    q = add(q, div(R, N));
+    q = add(q, mul(R, rN));
   }
-  for (int it = 0; it < 4; ++it) {
+  for (int it = 0; it < 6; ++it) {
     const uint32_t qb = bits(q);
     const float p = mul(q, N);
     const float e = fma(q, N, -p);  // q N - p, exact

@@ -13,7 +13,8 @@ int main() {
     std::memcpy(&hi, &hb, 4);
     std::memcpy(&lo, &lb, 4);
     bool ok = false;
-    const float q = vgicp::mean_rn32(hi, lo, n, ok);
+    const volatile float rN = 1.0f / (float)n;  // RN32(1 / n)
+    const float q = vgicp::mean_rn32(hi, lo, n, rN, ok);
     unsigned qb;
     std::memcpy(&qb, &q, 4);
     std::printf("%d %08x\n", ok ? 1 : 0, qb);

@@ -419,3 +419,40 @@ def test_rebuild_with_more_voxels_keeps_parity(dev):
     lin = api.linearize(vm, cu(src), cu(covs[::3]), T)
     refl = oracle.linearize(ref, src, covs[::3], T)
     check_factor(lin.out, lin.inliers, refl, "after rebuild")
+
+
+@pytest.mark.gpu
+def test_rebuilds_leave_no_stale_table_entries(dev):
+    """A rebuild empties only the table slots of the previous build's voxels.
+    Alternating clouds with many and few voxels must give, after every rebuild,
+    exactly the maps and factors of a fresh build: a slot left behind would add
+    hits (inliers) for voxels the new cloud does not have."""
+    rng = np.random.default_rng(31)
+    n, K, r = 5000, 3, 0.5
+    sparse = (rng.random((K * n, 3)) * 14.0 - 7.0).astype(np.float32)
+    dense = (rng.normal(size=(K * n, 3)) * 0.7).astype(np.float32)
+    covs = np.tile(np.array([0.02, 0, 0, 0.02, 0, 0.02], np.float32), (K * n, 1))
+    off = np.arange(K + 1, dtype=np.int64) * n
+    probe = (rng.random((4000, 3)) * 14.0 - 7.0).astype(np.float32)
+    pcov = np.tile(np.array([0.02, 0, 0, 0.02, 0, 0.02], np.float32), (4000, 1))
+    pairs = np.array([[m, 0] for m in range(K)], np.int32)
+    poses = np.stack([np.eye(4)] * K)
+    srcs = [(cu(probe), cu(pcov))]
+    maps = api.build_voxelmaps(cu(sparse), cu(covs), off, r)
+    for cloud in (dense, sparse, dense, sparse):
+        api.rebuild_voxelmaps(maps, cu(cloud), cu(covs))
+        fresh = api.build_voxelmaps(cu(cloud), cu(covs), off, r)
+        for a, b in zip(maps, fresh):
+            a.status()
+            ea, eb = a.export(), b.export()
+            for k in ea:
+                assert np.array_equal(ea[k], eb[k]), k
+        got = api.linearize_batched(maps, srcs, pairs, poses)
+        ref = api.linearize_batched(fresh, srcs, pairs, poses)
+        assert torch.equal(got.out, ref.out) and torch.equal(got.inliers, ref.inliers)
+        ring = [[m, (m + 1) % K] for m in range(K)]  # the maps' grouped clouds as sources
+        got = api.linearize_batched(maps, maps, ring, poses)
+        ref = api.linearize_batched(fresh, fresh, ring, poses)
+        assert torch.equal(got.out, ref.out) and torch.equal(got.inliers, ref.inliers)
+        for b in fresh:
+            b.close()
