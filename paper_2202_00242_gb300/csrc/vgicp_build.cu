@@ -4,7 +4,8 @@
 //
 // Pipeline for a batch of maps built from concatenated clouds (one launch per
 // step for the whole batch):
-//   init      table slots <- empty
+//   reset     table slots <- empty: every slot on the first build, afterwards
+//             only the slots the previous build's voxels occupy
 //   insert    per point: exact key, open-addressing insert (CAS on the 64-bit
 //             key, bounded linear probe), count, smallest point index
 //   first     per point: 1 if it is the smallest index of its voxel
@@ -14,11 +15,12 @@
 //   sort      per map chunk: the voxels in Morton order of their keys (rank)
 //   scan      offsets of the voxels' point lists, in rank order
 //   scatter   per point: append its index to its voxel's list
+//   capacity  per map: lookup-table capacity from the voxel count
 //   finalize  per voxel, in rank order: sort its list, sum means and
 //             covariances (exactly, else in binary64 in ascending point index),
 //             divide by N, round to float32; copy the points into the voxel-
-//             grouped cloud (the lists laid end to end)
-//   lookup    per map: lookup table (inline records) from the finished voxels
+//             grouped cloud (the lists laid end to end); insert the voxel into
+//             its map's lookup table (inline records)
 // The result is deterministic and bit-identical to the binary64 definition
 // rounded once to float32.
 #include <cuda_runtime.h>
@@ -208,6 +210,71 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
   }
 }
 
+// Inserts voxel v (its key, count, mean and the Cholesky factor of its
+// covariance) into its map's lookup table: linear probing from the key's home
+// slot, claiming a slot with a CAS on the key; a key placed past its home sets
+// the home slot's spill flag.  lslot_of[v] records the slot (kNoSlot if the
+// probe limit was reached, which is reported as VGICP_ERR_HASH_FULL).
+__device__ __forceinline__ void insert_lookup(uint32_t v, unsigned long long key, uint32_t c,
+                                              const float* q, int32_t n_maps,
+                                              const uint32_t* __restrict__ vbase,
+                                              const int64_t* __restrict__ slot_base,
+                                              const uint32_t* __restrict__ vmask,
+                                              int32_t max_probe, VSlot* vslots,
+                                              uint32_t* __restrict__ lslot_of, int32_t* status) {
+  int lo = 0, hi = n_maps;  // last m with vbase[m] <= v
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (vbase[mid] <= v) lo = mid; else hi = mid;
+  }
+  const unsigned long long fm = (1ull << kKeyBits) - 1ull;
+  const int kx = (int)((key >> (2 * kKeyBits)) & fm) - kKeyBias;
+  const int ky = (int)((key >> kKeyBits) & fm) - kKeyBias;
+  const int kz = (int)(key & fm) - kKeyBias;
+  const uint32_t mask = vmask[lo];
+  VSlot* t = vslots + slot_base[lo];
+  const uint32_t home = hash_key(kx, ky, kz) & mask;
+  uint32_t h = home;
+  bool placed = false;
+  for (int p = 0; p < max_probe; ++p) {
+    if (atomicCAS(&t[h].key, kEmptyKey, key) == kEmptyKey) {
+      placed = true;
+      break;
+    }
+    h = (h + 1) & mask;
+  }
+  if (placed && h != home) atomicOr(&t[home].spill, 1u);
+  lslot_of[v] = placed ? (uint32_t)(slot_base[lo] + h) : kNoSlot;
+  if (!placed) {
+    set_status(status, VGICP_ERR_HASH_FULL);
+    return;
+  }
+  VSlot& sl = t[h];
+  sl.vid = v;
+  sl.count = c;
+  sl.mu[0] = q[0];
+  sl.mu[1] = q[1];
+  sl.mu[2] = q[2];
+  // the Cholesky factor L of C' (the linearization forms R^T C' R as (R^T L)(R^T L)^T);
+  // a non-positive pivot (a semi-definite C') leaves its column zero
+  const float l00 = q[3] > 0.f ? sqrtf(q[3]) : 0.f;
+  const float il0 = l00 > 0.f ? 1.0f / l00 : 0.f;
+  const float l10 = q[4] * il0, l20 = q[5] * il0;
+  const float p11 = q[6] - l10 * l10;
+  const float l11 = p11 > 0.f ? sqrtf(p11) : 0.f;
+  const float l21 = l11 > 0.f ? (q[7] - l20 * l10) / l11 : 0.f;
+  const float p22 = q[8] - l20 * l20 - l21 * l21;
+  const float l22 = p22 > 0.f ? sqrtf(p22) : 0.f;
+  sl.cov[0] = l00;
+  sl.cov[1] = l10;
+  sl.cov[2] = l20;
+  sl.cov[3] = l11;
+  sl.cov[4] = l21;
+  sl.cov[5] = l22;
+  sl.pad1[0] = 0.0f;
+  sl.pad1[1] = 0.0f;
+}
+
 // Per-voxel sums and the grouped cloud.  A CTA takes 128 consecutive ranks,
 // whose point lists are one contiguous segment of plist:
 //   1. the segment is loaded into shared memory (coalesced) and each thread
@@ -237,7 +304,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     int64_t n_max, const uint32_t* __restrict__ n_vox, const float* __restrict__ pts,
     const float* __restrict__ covs, const uint32_t* __restrict__ vcount,
     const uint32_t* __restrict__ vorder, const uint32_t* __restrict__ goff,
-    uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gpts, float* gcovs) {
+    uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gpts, float* gcovs,
+    const unsigned long long* __restrict__ vkeys, int32_t n_maps,
+    const uint32_t* __restrict__ vbase, const int64_t* __restrict__ slot_base,
+    const uint32_t* __restrict__ vmask, int32_t max_probe, VSlot* vslots,
+    uint32_t* __restrict__ lslot_of, int32_t* status) {
   __shared__ uint32_t stage[kFinStage];
   const int64_t V = min((int64_t)*n_vox, n_max);
   for (int64_t r0 = (int64_t)blockIdx.x * kFinThreads; r0 < V; r0 += (int64_t)gridDim.x * kFinThreads) {
@@ -334,6 +405,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
       recs[3 * v + 0] = make_float4(q[0], q[1], q[2], __uint_as_float(c));
       recs[3 * v + 1] = make_float4(q[3], q[4], q[5], q[6]);
       recs[3 * v + 2] = make_float4(q[7], q[8], 0.0f, 0.0f);
+      insert_lookup(v, vkeys[v], c, q, n_maps, vbase, slot_base, vmask, max_probe, vslots,
+                    lslot_of, status);
     }
     __syncthreads();  // the stage is reused by the next batch
   }
@@ -506,74 +579,6 @@ __global__ void vslot_init_kernel(const int64_t* __restrict__ slot_base,
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) vmask[m] = cap - 1u;
-}
-
-// Per voxel: insert key and Gaussian into its map's lookup table.
-__global__ void vslot_insert_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
-                                    int32_t n_maps, const uint32_t* __restrict__ vbase,
-                                    const int64_t* __restrict__ slot_base,
-                                    const uint32_t* __restrict__ vmask,
-                                    const unsigned long long* __restrict__ vkeys,
-                                    const float4* __restrict__ recs, int32_t max_probe,
-                                    VSlot* vslots, uint32_t* __restrict__ lslot_of,
-                                    int32_t* status) {
-  const int64_t V = *n_vox;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = n_maps;  // last m with vbase[m] <= v
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (vbase[mid] <= (uint32_t)v) lo = mid; else hi = mid;
-    }
-    const unsigned long long key = vkeys[v];
-    const unsigned long long fm = (1ull << kKeyBits) - 1ull;
-    const int kx = (int)((key >> (2 * kKeyBits)) & fm) - kKeyBias;
-    const int ky = (int)((key >> kKeyBits) & fm) - kKeyBias;
-    const int kz = (int)(key & fm) - kKeyBias;
-    const uint32_t mask = vmask[lo];
-    VSlot* t = vslots + slot_base[lo];
-    const uint32_t home = hash_key(kx, ky, kz) & mask;
-    uint32_t h = home;
-    bool placed = false;
-    for (int p = 0; p < max_probe; ++p) {
-      if (atomicCAS(&t[h].key, kEmptyKey, key) == kEmptyKey) {
-        placed = true;
-        break;
-      }
-      h = (h + 1) & mask;
-    }
-    if (placed && h != home) atomicOr(&t[home].spill, 1u);
-    lslot_of[v] = placed ? (uint32_t)(slot_base[lo] + h) : kNoSlot;
-    if (!placed) {
-      set_status(status, VGICP_ERR_HASH_FULL);
-      continue;
-    }
-    const float4 r0 = recs[3 * v], r1 = recs[3 * v + 1], r2 = recs[3 * v + 2];
-    VSlot& sl = t[h];
-    sl.vid = (uint32_t)v;
-    sl.count = __float_as_uint(r0.w);
-    sl.mu[0] = r0.x;
-    sl.mu[1] = r0.y;
-    sl.mu[2] = r0.z;
-    // the Cholesky factor L of C' (the linearization forms R^T C' R as (R^T L)(R^T L)^T);
-    // a non-positive pivot (a semi-definite C') leaves its column zero
-    const float l00 = r1.x > 0.f ? sqrtf(r1.x) : 0.f;
-    const float il0 = l00 > 0.f ? 1.0f / l00 : 0.f;
-    const float l10 = r1.y * il0, l20 = r1.z * il0;
-    const float p11 = r1.w - l10 * l10;
-    const float l11 = p11 > 0.f ? sqrtf(p11) : 0.f;
-    const float l21 = l11 > 0.f ? (r2.x - l20 * l10) / l11 : 0.f;
-    const float p22 = r2.y - l20 * l20 - l21 * l21;
-    const float l22 = p22 > 0.f ? sqrtf(p22) : 0.f;
-    sl.cov[0] = l00;
-    sl.cov[1] = l10;
-    sl.cov[2] = l20;
-    sl.cov[3] = l11;
-    sl.cov[4] = l21;
-    sl.cov[5] = l22;
-    sl.pad1[0] = 0.0f;
-    sl.pad1[1] = 0.0f;
-  }
 }
 
 // ---- exclusive scan of uint32 (three phases) --------------------------------
@@ -810,9 +815,6 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
   scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of, s->d_vfill,
                                          s->d_plist);
-  finalize_kernel<<<g, kFinThreads, 0, st>>>(n, s->d_num_voxels, points, covs, s->d_vcount,
-                                             vorder, s->d_goff, s->d_plist, s->d_recs,
-                                             s->d_gpts, s->d_gcovs);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
     max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);
@@ -822,14 +824,15 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   vslot_init_kernel<<<dim3(gx, s->n_maps), kThreads, 0, st>>>(s->d_vslot_base, s->d_vbase,
                                                              s->d_vslots, s->d_vmask,
                                                              was_built ? 0 : 1);
-  vslot_insert_kernel<<<g, kThreads, 0, st>>>(n, s->d_num_voxels, s->n_maps, s->d_vbase,
-                                              s->d_vslot_base, s->d_vmask, s->d_vkeys, s->d_recs,
-                                              s->max_probe, s->d_vslots, s->d_lslot_of,
-                                              s->d_status);
+  // sums, records, grouped clouds and the lookup tables
+  finalize_kernel<<<g, kFinThreads, 0, st>>>(
+      n, s->d_num_voxels, points, covs, s->d_vcount, vorder, s->d_goff, s->d_plist, s->d_recs,
+      s->d_gpts, s->d_gcovs, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
+      s->max_probe, s->d_vslots, s->d_lslot_of, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, first, assign, vbase, sort, rank counts, list bases, scatter, finalize,
-  // vslot init/insert (+ reset or init: 1)
-  count_launches(11);
+  // insert, first, assign, vbase, sort, rank counts, list bases, scatter, vslot init,
+  // finalize (+ reset or init: 1)
+  count_launches(10);
   s->built = true;
   return VGICP_OK;
 }
