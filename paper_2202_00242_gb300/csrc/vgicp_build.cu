@@ -4,8 +4,9 @@
 //
 // Pipeline for a batch of maps built from concatenated clouds (one launch per
 // step for the whole batch):
-//   reset     table slots <- empty: every slot on the first build, afterwards
-//             only the slots the previous build's voxels occupy
+//   reset     table slots <- empty: every slot on the first build; afterwards
+//             the lookup-table slots the previous build's voxels occupy (the
+//             build table is left empty by the scatter)
 //   insert    per point: exact key, open-addressing insert (CAS on the 64-bit
 //             key, bounded linear probe), count, smallest point index
 //   first     per point: 1 if it is the smallest index of its voxel
@@ -14,7 +15,8 @@
 //   assign    per first point: voxel count, key; slot.vid <- voxel id
 //   sort      per map chunk: the voxels in Morton order of their keys (rank)
 //   scan      offsets of the voxels' point lists, in rank order
-//   scatter   per point: append its index to its voxel's list
+//   scatter   per point: append its index to its voxel's list; the voxel's
+//             last point empties its build-table slot
 //   capacity  per map: lookup-table capacity from the voxel count
 //   finalize  per voxel, in rank order: sort its list, sum means and
 //             covariances (exactly, else in binary64 in ascending point index),
@@ -139,36 +141,27 @@ __global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_
 __global__ void assign_kernel(int64_t n_total, const uint32_t* __restrict__ first,
                               const uint32_t* __restrict__ vid, const uint32_t* __restrict__ pt_slot,
                               Slot* slots, uint32_t* __restrict__ vcount,
-                              unsigned long long* __restrict__ vkeys,
-                              uint32_t* __restrict__ hslot_of) {
+                              unsigned long long* __restrict__ vkeys) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!first[i]) continue;
     const uint32_t v = vid[i];
-    const uint32_t hs = pt_slot[i];
-    Slot* s = slots + hs;
+    Slot* s = slots + pt_slot[i];
     vcount[v] = s->count;
     vkeys[v] = s->key;
     s->vid = v;
-    hslot_of[v] = hs;
   }
 }
 
-// Rebuild: empty the build-table and lookup-table slots the previous build's
-// voxels occupy (every slot a build claims belongs to one of its voxels, and
-// spill flags are set only on claimed slots), which leaves both tables empty.
+// Rebuild: empty the lookup-table slots the previous build's voxels occupy
+// (every slot a build claims belongs to one of its voxels, and spill flags are
+// set only on claimed slots), which leaves the tables empty.  (The build table
+// is emptied by the scatter of every build.)
 __global__ void reset_tables_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
-                                    const uint32_t* __restrict__ hslot_of,
-                                    const uint32_t* __restrict__ lslot_of, Slot* slots,
-                                    VSlot* vslots) {
+                                    const uint32_t* __restrict__ lslot_of, VSlot* vslots) {
   const int64_t V = *n_vox;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
        v += (int64_t)gridDim.x * blockDim.x) {
-    Slot e;
-    e.key = kEmptyKey;
-    e.vid = 0xFFFFFFFFu;
-    e.count = 0u;
-    slots[hslot_of[v]] = e;
     const uint32_t ls = lslot_of[v];
     if (ls != kNoSlot)
       asm volatile("st.global.v8.b32 [%0], {%1, %1, %2, %2, %2, %2, %2, %2};" ::"l"(vslots + ls),
@@ -197,16 +190,30 @@ __global__ void list_base_kernel(int64_t n_max, const uint32_t* __restrict__ n_v
     base[v] = goff[vrank[v]];
 }
 
-__global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot,
-                               const Slot* __restrict__ slots, const uint32_t* __restrict__ base,
-                               uint32_t* vfill, uint32_t* __restrict__ plist) {
+// Per point: append its index to its voxel's list.  The voxel's last point
+// (the one whose fill count reaches the voxel's count; every other point of the
+// voxel has read the slot before its own increment) empties the build-table
+// slot, whose sector it has just read: the build table is empty again when the
+// scatter ends, ready for the next build.
+__global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot, Slot* slots,
+                               const uint32_t* __restrict__ base,
+                               const uint32_t* __restrict__ vcount, uint32_t* vfill,
+                               uint32_t* __restrict__ plist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = pt_slot[i];
     if (s == kNoSlot) continue;
     const uint32_t v = slots[s].vid;
-    const uint32_t pos = base[v] + atomicAdd(vfill + v, 1u);
-    plist[pos] = (uint32_t)i;
+    const uint32_t c = vcount[v];
+    const uint32_t f = atomicAdd(vfill + v, 1u);
+    plist[base[v] + f] = (uint32_t)i;
+    if (f + 1u == c) {
+      Slot e;
+      e.key = kEmptyKey;
+      e.vid = 0xFFFFFFFFu;
+      e.count = 0u;
+      slots[s] = e;
+    }
   }
 }
 
@@ -745,8 +752,8 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   s->built = false;
   if (was_built) {
     // empty the slots of the previous build's voxels
-    reset_tables_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, s->d_hslot_of,
-                                                 s->d_lslot_of, s->d_slots, s->d_vslots);
+    reset_tables_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, s->d_lslot_of,
+                                                 s->d_vslots);
     count_launches(1);
   } else if (s->cap_total > 0) {
     init_slots_kernel<<<grid_for(s->cap_total, kThreads), kThreads, 0, st>>>(s->d_slots,
@@ -780,7 +787,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   int rc = launch_exclusive_scan(first, s->d_flag, n, nullptr, s->d_scan_tmp, s->d_num_voxels, st);
   if (rc != VGICP_OK) return rc;
   assign_kernel<<<g, kThreads, 0, st>>>(n, first, s->d_flag, s->d_pt_slot, s->d_slots,
-                                        s->d_vcount, s->d_vkeys, s->d_hslot_of);
+                                        s->d_vcount, s->d_vkeys);
   vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
                                                             s->d_flag, s->d_num_voxels,
                                                             s->d_vbase);
@@ -813,8 +820,8 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   list_base_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_goff,
                                             s->d_vslot_of);
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
-  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of, s->d_vfill,
-                                         s->d_plist);
+  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of,
+                                         s->d_vcount, s->d_vfill, s->d_plist);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
     max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);

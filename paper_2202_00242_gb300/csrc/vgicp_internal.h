@@ -59,11 +59,11 @@ struct MapSet {
   uint32_t* d_vfill = nullptr;    // n_total: first-point flags, counts by rank, list fill
   uint32_t* d_plist = nullptr;    // n_total: point lists of the voxels, in rank order
   uint32_t* d_vslot_of = nullptr; // n_total: list base of each voxel
-  // kept from one build to the next: the table slots each voxel occupies, so a
-  // rebuild empties just those (every other slot is empty already)
-  uint32_t* d_hslot_of = nullptr; // n_total: build-table slot of each voxel
+  // kept from one build to the next: the lookup-table slot each voxel occupies,
+  // so a rebuild empties just those (every other slot is empty already)
   uint32_t* d_lslot_of = nullptr; // n_total: lookup-table slot of each voxel (or kNoSlot)
-  bool built = false;             // a build has run: the tables hold only its voxels
+  bool built = false;             // a build has run: the lookup tables hold only its
+                                  // voxels and the build table is empty
   float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
   float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
   uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
