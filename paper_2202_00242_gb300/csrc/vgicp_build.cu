@@ -11,8 +11,9 @@
 //             key, bounded linear probe), count, smallest point index
 //   first     per point: 1 if it is the smallest index of its voxel
 //   scan      voxel id = number of first points before it (so voxels are
-//             numbered in order of first appearance, map by map)
-//   assign    per first point: voxel count, key; slot.vid <- voxel id
+//             numbered in order of first appearance, map by map); its last
+//             pass gives each first point's voxel its count, key and, in the
+//             slot, its id
 //   sort      per map chunk: the voxels in Morton order of their keys (rank)
 //   scan      offsets of the voxels' point lists, in rank order
 //   scatter   per point: append its index to its voxel's list; the voxel's
@@ -138,20 +139,6 @@ __global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_
   }
 }
 
-__global__ void assign_kernel(int64_t n_total, const uint32_t* __restrict__ first,
-                              const uint32_t* __restrict__ vid, const uint32_t* __restrict__ pt_slot,
-                              Slot* slots, uint32_t* __restrict__ vcount,
-                              unsigned long long* __restrict__ vkeys) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (!first[i]) continue;
-    const uint32_t v = vid[i];
-    Slot* s = slots + pt_slot[i];
-    vcount[v] = s->count;
-    vkeys[v] = s->key;
-    s->vid = v;
-  }
-}
 
 // Rebuild: empty the lookup-table slots the previous build's voxels occupy
 // (every slot a build claims belongs to one of its voxels, and spill flags are
@@ -308,8 +295,8 @@ __device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
 }
 
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
-    int64_t n_max, const uint32_t* __restrict__ n_vox, const float* __restrict__ pts,
-    const float* __restrict__ covs, const uint32_t* __restrict__ vcount,
+    int64_t n_max, const uint32_t* __restrict__ n_vox, const uint32_t* __restrict__ n_valid,
+    const float* __restrict__ pts, const float* __restrict__ covs,
     const uint32_t* __restrict__ vorder, const uint32_t* __restrict__ goff,
     uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gpts, float* gcovs,
     const unsigned long long* __restrict__ vkeys, int32_t n_maps,
@@ -318,17 +305,19 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     uint32_t* __restrict__ lslot_of, int32_t* status) {
   __shared__ uint32_t stage[kFinStage];
   const int64_t V = min((int64_t)*n_vox, n_max);
+  const uint32_t total = *n_valid;  // end of the last list (goff[V] is not stored)
   for (int64_t r0 = (int64_t)blockIdx.x * kFinThreads; r0 < V; r0 += (int64_t)gridDim.x * kFinThreads) {
     const int64_t r1 = min(V, r0 + kFinThreads);
+    // list bounds from consecutive offsets: no dependent load through vorder
     const uint32_t seg0 = goff[r0];
-    const uint32_t seg1 = goff[r1 - 1] + vcount[vorder[r1 - 1]];
+    const uint32_t seg1 = r1 < V ? goff[r1] : total;
     const uint32_t len = seg1 - seg0;
     const bool staged = len <= (uint32_t)kFinStage;
     const int64_t r = r0 + threadIdx.x;
     const bool mine = r < r1;
     const uint32_t v = mine ? vorder[r] : 0u;
-    const uint32_t c = mine ? vcount[v] : 0u;
     const uint32_t o = mine ? goff[r] : 0u;
+    const uint32_t c = mine ? (r + 1 < V ? goff[r + 1] : total) - o : 0u;
     // 1. sort the lists by point index
     if (staged) {
       for (uint32_t i = threadIdx.x; i < len; i += kFinThreads) stage[i] = plist[seg0 + i];
@@ -369,8 +358,24 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
         const float2* gc = reinterpret_cast<const float2*>(gcovs + 6 * d);
         const float2 c0 = gc[0], c1 = gc[1], c2 = gc[2];
         f[3] = c0.x; f[4] = c0.y; f[5] = c1.x; f[6] = c1.y; f[7] = c2.x; f[8] = c2.y;
+        // hi + lo stays the exact sum while each TwoSum error adds exactly to lo
+        // (checked); renormalised once at the end
 #pragma unroll
-        for (int k = 0; k < 9; ++k) df_add(hi[k], lo[k], f[k], exact);
+        for (int k = 0; k < 9; ++k) {
+          float t, e, u, e2;
+          two_sum(hi[k], f[k], t, e);
+          two_sum(lo[k], e, u, e2);
+          exact = exact && (e2 == 0.0f);
+          hi[k] = t;
+          lo[k] = u;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {  // hi = RN(hi + lo), lo = the exact remainder
+        float t, e;
+        two_sum(hi[k], lo[k], t, e);
+        hi[k] = t;
+        lo[k] = e;
       }
       // q = RN32(RN64(sum / N)) per component: from the exact float pair in
       // float32 where certified, else (rare) from the binary64 definition
@@ -597,10 +602,12 @@ __device__ __forceinline__ int64_t scan_len(int64_t n_max, const uint32_t* n_dev
   return n_dev ? min(n_max, (int64_t)*n_dev) : n_max;
 }
 
-// Block-wide exclusive scan of one value per thread; returns the thread's
-// exclusive prefix and writes the block total to *total.
+// Block-wide exclusive scan of one value per thread (T threads); returns the
+// thread's exclusive prefix and writes the block total to *total.
+template <int T>
 __device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t* total) {
-  __shared__ uint32_t warp_sum[kScanThreads / 32];
+  static_assert(T % 32 == 0 && T <= 1024, "block size");
+  __shared__ uint32_t warp_sum[T / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t inc = x;
 #pragma unroll
@@ -611,15 +618,15 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t* total)
   if (lane == 31) warp_sum[w] = inc;
   __syncthreads();
   if (w == 0) {
-    uint32_t ws = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
+    uint32_t ws = lane < T / 32 ? warp_sum[lane] : 0u;
     uint32_t wi = ws;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
       if (lane >= o) wi += y;
     }
-    if (lane < kScanThreads / 32) warp_sum[lane] = wi - ws;
-    if (lane == kScanThreads / 32 - 1) *total = wi;
+    if (lane < T / 32) warp_sum[lane] = wi - ws;
+    if (lane == T / 32 - 1) *total = wi;
   }
   __syncthreads();
   uint32_t r = warp_sum[w] + inc - x;
@@ -636,23 +643,26 @@ __global__ void scan_tile_sums_kernel(const uint32_t* __restrict__ in, int64_t n
   for (int k = 0; k < kScanPerThread; ++k)
     if (base + k < n) s += in[base + k];
   __shared__ uint32_t total;
-  block_exclusive(s, &total);
+  block_exclusive<kScanThreads>(s, &total);
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void scan_sums_kernel(uint32_t* __restrict__ sums, int64_t nb,
-                                 uint32_t* __restrict__ total_dev) {
-  __shared__ uint32_t chunk_total;
-  uint32_t carry = 0;
-  for (int64_t c = 0; c < nb; c += kScanThreads) {
-    const int64_t i = c + threadIdx.x;
-    uint32_t x = i < nb ? sums[i] : 0u;
-    uint32_t e = block_exclusive(x, &chunk_total);
-    if (i < nb) sums[i] = carry + e;
-    carry += chunk_total;
-    __syncthreads();
+// One CTA: each thread scans a contiguous run of the tile sums.
+constexpr int kScanSumsThreads = 1024;
+__global__ void __launch_bounds__(kScanSumsThreads) scan_sums_kernel(
+    uint32_t* __restrict__ sums, int64_t nb, uint32_t* __restrict__ total_dev) {
+  __shared__ uint32_t total;
+  const int64_t per = (nb + kScanSumsThreads - 1) / kScanSumsThreads;
+  const int64_t a = min(nb, (int64_t)threadIdx.x * per), b = min(nb, a + per);
+  uint32_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += sums[i];
+  uint32_t run = block_exclusive<kScanSumsThreads>(s, &total);
+  for (int64_t i = a; i < b; ++i) {
+    const uint32_t x = sums[i];
+    sums[i] = run;
+    run += x;
   }
-  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+  if (threadIdx.x == 0 && total_dev) *total_dev = total;
 }
 
 __global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_max,
@@ -667,11 +677,45 @@ __global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_m
     s += v[k];
   }
   __shared__ uint32_t total;
-  uint32_t run = block_exclusive(s, &total) + sums[blockIdx.x];
+  uint32_t run = block_exclusive<kScanThreads>(s, &total) + sums[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanPerThread; ++k) {
     if (base + k < n) out[base + k] = run;
     run += v[k];
+  }
+}
+
+// Third pass of the first-appearance scan fused with the voxel assignment:
+// ids[i] = number of first points before point i, and each first point (the
+// smallest index of its voxel) gives its voxel that id: the voxel's count and
+// key are recorded by id and the id replaces the index in the build-table slot.
+__global__ void scan_assign_kernel(const uint32_t* __restrict__ first, uint32_t* __restrict__ ids,
+                                   int64_t n, const uint32_t* __restrict__ sums,
+                                   const uint32_t* __restrict__ pt_slot, Slot* slots,
+                                   uint32_t* __restrict__ vcount,
+                                   unsigned long long* __restrict__ vkeys) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+  uint32_t f[kScanPerThread];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    f[k] = (base + k < n) ? first[base + k] : 0u;
+    s += f[k];
+  }
+  __shared__ uint32_t total;
+  uint32_t run = block_exclusive<kScanThreads>(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    if (base + k < n) {
+      ids[base + k] = run;
+      if (f[k]) {
+        Slot* sl = slots + pt_slot[base + k];
+        vcount[run] = sl->count;
+        vkeys[run] = sl->key;
+        sl->vid = run;
+      }
+    }
+    run += f[k];
   }
 }
 
@@ -695,7 +739,7 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max, cons
   }
   const int64_t nb = (n_max + kScanTile - 1) / kScanTile;
   scan_tile_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n_max, n_dev, block_tmp);
-  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(block_tmp, nb, total_dev);
+  scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(block_tmp, nb, total_dev);
   scan_tiles_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n_max, n_dev, block_tmp);
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(3);
@@ -778,16 +822,25 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   }
   const float inv_r = (float)(1.0 / s->resolution);
   const int g = grid_for(n, kThreads);
-  uint32_t* first = s->d_vfill;  // reused: dead after assign, then zeroed
+  uint32_t* first = s->d_vfill;  // reused: dead after the first scan, then zeroed
   insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->n_maps, s->d_slot_base,
                                         s->d_cap_mask, inv_r, s->resolution, s->max_probe,
                                         s->d_slots, s->d_pt_slot, s->d_status);
   first_kernel<<<g, kThreads, 0, st>>>(n, s->d_point_off, s->n_maps, s->d_slots, s->d_pt_slot,
                                        first);
-  int rc = launch_exclusive_scan(first, s->d_flag, n, nullptr, s->d_scan_tmp, s->d_num_voxels, st);
-  if (rc != VGICP_OK) return rc;
-  assign_kernel<<<g, kThreads, 0, st>>>(n, first, s->d_flag, s->d_pt_slot, s->d_slots,
-                                        s->d_vcount, s->d_vkeys);
+  // voxel ids in order of first appearance (scan of the first flags), assigned
+  // to the voxels in the scan's last pass
+  int rc = VGICP_OK;
+  {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    scan_tile_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(first, n, nullptr,
+                                                                 s->d_scan_tmp);
+    scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(s->d_scan_tmp, nb, s->d_num_voxels);
+    scan_assign_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
+        first, s->d_flag, n, s->d_scan_tmp, s->d_pt_slot, s->d_slots, s->d_vcount, s->d_vkeys);
+    VGICP_CUDA_TRY(cudaGetLastError());
+    count_launches(3);
+  }
   vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
                                                             s->d_flag, s->d_num_voxels,
                                                             s->d_vbase);
@@ -798,7 +851,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   // Morton order of the voxels (chunks of a map), the list offsets in that order,
   // the lists, then the per-voxel sums (which also write the grouped clouds).
   // d_flag (voxel id per first point) is dead after vbase, d_vfill (first flags)
-  // after assign.
+  // after the first scan.
   uint32_t* vrank = s->d_flag;
   uint32_t* vorder = s->d_voff;
   uint32_t* gcount = s->d_vfill;
@@ -833,13 +886,13 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
                                                              was_built ? 0 : 1);
   // sums, records, grouped clouds and the lookup tables
   finalize_kernel<<<g, kFinThreads, 0, st>>>(
-      n, s->d_num_voxels, points, covs, s->d_vcount, vorder, s->d_goff, s->d_plist, s->d_recs,
+      n, s->d_num_voxels, s->d_num_valid, points, covs, vorder, s->d_goff, s->d_plist, s->d_recs,
       s->d_gpts, s->d_gcovs, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
       s->max_probe, s->d_vslots, s->d_lslot_of, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, first, assign, vbase, sort, rank counts, list bases, scatter, vslot init,
-  // finalize (+ reset or init: 1)
-  count_launches(10);
+  // insert, first, vbase, sort, rank counts, list bases, scatter, vslot init, finalize
+  // (+ reset or init: 1; the two scans: 3 each)
+  count_launches(9);
   s->built = true;
   return VGICP_OK;
 }
