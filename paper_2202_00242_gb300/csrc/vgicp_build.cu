@@ -9,13 +9,13 @@
 //             build table is left empty by the scatter)
 //   insert    per point: exact key, open-addressing insert (CAS on the 64-bit
 //             key, bounded linear probe), count, smallest point index
-//   first     per point: 1 if it is the smallest index of its voxel
-//   scan      voxel id = number of first points before it (so voxels are
+//   scan      first flags (1 if a point is the smallest index of its voxel),
+//             voxel id = number of first points before it (so voxels are
 //             numbered in order of first appearance, map by map); its last
 //             pass gives each first point's voxel its count, key and, in the
 //             slot, its id
 //   sort      per map chunk: the voxels in Morton order of their keys (rank)
-//   scan      offsets of the voxels' point lists, in rank order
+//   scan      offsets of the voxels' point lists, in rank order and by voxel
 //   scatter   per point: append its index to its voxel's list; the voxel's
 //             last point empties its build-table slot
 //   capacity  per map: lookup-table capacity from the voxel count
@@ -89,7 +89,6 @@ __global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int m = find_map_warp(point_off, n_maps, i);
-    const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
     const int kx = axis_key_target(__ldg(pts + 3 * i + 0), inv_r, r);
     const int ky = axis_key_target(__ldg(pts + 3 * i + 1), inv_r, r);
     const int kz = axis_key_target(__ldg(pts + 3 * i + 2), inv_r, r);
@@ -118,26 +117,11 @@ __global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
       continue;
     }
     atomicAdd(&slots[found].count, 1u);
-    atomicMin(&slots[found].vid, li);
+    atomicMin(&slots[found].vid, (uint32_t)i);
     pt_slot[i] = found;
   }
 }
 
-__global__ void first_kernel(int64_t n_total, const int64_t* __restrict__ point_off,
-                             int32_t n_maps, const Slot* __restrict__ slots,
-                             const uint32_t* __restrict__ pt_slot, uint32_t* __restrict__ first) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = pt_slot[i];
-    uint32_t f = 0;
-    if (s != kNoSlot) {
-      const int m = find_map_warp(point_off, n_maps, i);
-      const uint32_t li = (uint32_t)(i - __ldg(point_off + m));
-      f = (slots[s].vid == li) ? 1u : 0u;
-    }
-    first[i] = f;
-  }
-}
 
 
 // Rebuild: empty the lookup-table slots the previous build's voxels occupy
@@ -166,16 +150,6 @@ __global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __r
   vbase[m] = (o < n_total) ? vid[o] : *n_vox;
 }
 
-// Per voxel: the base of its point list (the grouped offset of its rank), in
-// voxel order, so that the scatter needs one indirection less.
-__global__ void list_base_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
-                                 const uint32_t* __restrict__ vrank,
-                                 const uint32_t* __restrict__ goff, uint32_t* __restrict__ base) {
-  const int64_t V = *n_vox;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
-       v += (int64_t)gridDim.x * blockDim.x)
-    base[v] = goff[vrank[v]];
-}
 
 // Per point: append its index to its voxel's list.  The voxel's last point
 // (the one whose fill count reaches the voxel's count; every other point of the
@@ -442,8 +416,8 @@ __device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
 }
 
 // One CTA per (map, chunk): bitonic sort of the chunk's voxels by Morton code in
-// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order
-// and vorder[rank] = v.
+// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order,
+// vorder[rank] = v and gcount[rank] = the voxel's point count.
 //
 // Element i lives at i + i / 16 (one pad word per 16), which keeps every access
 // pattern below free of bank conflicts.  Each pass loads a group of up to 16
@@ -488,8 +462,8 @@ __device__ __forceinline__ void bitonic_pass(unsigned long long* sk, uint32_t N,
 
 __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
-    const unsigned long long* __restrict__ vkeys, uint32_t* __restrict__ vrank,
-    uint32_t* __restrict__ vorder) {
+    const unsigned long long* __restrict__ vkeys, const uint32_t* __restrict__ vcount,
+    uint32_t* __restrict__ vrank, uint32_t* __restrict__ vorder, uint32_t* __restrict__ gcount) {
   extern __shared__ unsigned long long sk[];
   const int m = chunks[blockIdx.x].x;
   const uint32_t V = vbase[m + 1] - vbase[m];
@@ -500,6 +474,7 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     vrank[vbase[m] + lo + i] = vbase[m] + lo + i;
     vorder[vbase[m] + lo + i] = vbase[m] + lo + i;
+    gcount[vbase[m] + lo + i] = vcount[vbase[m] + lo + i];
   }
   return;
 #endif
@@ -549,18 +524,10 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const uint32_t v = first + (uint32_t)(sk[sort_phys(i)] & 0xFFFFFFFFull);
     vrank[v] = first + i;
     vorder[first + i] = v;
+    gcount[first + i] = vcount[v];
   }
 }
 
-__global__ void rank_counts_kernel(int64_t n_max, const uint32_t* __restrict__ n_vox,
-                                   const uint32_t* __restrict__ vrank,
-                                   const uint32_t* __restrict__ vcount,
-                                   uint32_t* __restrict__ gcount) {
-  const int64_t V = *n_vox;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V && v < n_max;
-       v += (int64_t)gridDim.x * blockDim.x)
-    gcount[vrank[v]] = vcount[v];
-}
 
 
 __device__ __forceinline__ uint32_t lookup_capacity(uint32_t nvox) {
@@ -647,6 +614,28 @@ __global__ void scan_tile_sums_kernel(const uint32_t* __restrict__ in, int64_t n
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
+// First pass of the first-appearance scan: first[i] = 1 if point i is the
+// smallest index of its voxel (the build-table slot holds that index), and the
+// tile sums of these flags.
+__global__ void first_sums_kernel(const uint32_t* __restrict__ pt_slot,
+                                  const Slot* __restrict__ slots, int64_t n,
+                                  uint32_t* __restrict__ first, uint32_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+  uint32_t ps[kScanPerThread];
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) ps[k] = (base + k < n) ? pt_slot[base + k] : kNoSlot;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    const uint32_t f = (ps[k] != kNoSlot && slots[ps[k]].vid == (uint32_t)(base + k)) ? 1u : 0u;
+    if (base + k < n) first[base + k] = f;
+    s += f;
+  }
+  __shared__ uint32_t total;
+  block_exclusive<kScanThreads>(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
 // One CTA: each thread scans a contiguous run of the tile sums.
 constexpr int kScanSumsThreads = 1024;
 __global__ void __launch_bounds__(kScanSumsThreads) scan_sums_kernel(
@@ -716,6 +705,33 @@ __global__ void scan_assign_kernel(const uint32_t* __restrict__ first, uint32_t*
       }
     }
     run += f[k];
+  }
+}
+
+// Last pass of the scan of the rank-ordered counts: goff[r] = the offset of rank
+// r's list, also stored by voxel (base[vorder[r]]) for the scatter.
+__global__ void scan_lists_kernel(const uint32_t* __restrict__ gcount, uint32_t* __restrict__ goff,
+                                  int64_t n_max, const uint32_t* __restrict__ n_dev,
+                                  const uint32_t* __restrict__ sums,
+                                  const uint32_t* __restrict__ vorder, uint32_t* __restrict__ base) {
+  const int64_t n = scan_len(n_max, n_dev);
+  const int64_t b0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+  uint32_t v[kScanPerThread];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    v[k] = (b0 + k < n) ? gcount[b0 + k] : 0u;
+    s += v[k];
+  }
+  __shared__ uint32_t total;
+  uint32_t run = block_exclusive<kScanThreads>(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    if (b0 + k < n) {
+      goff[b0 + k] = run;
+      base[vorder[b0 + k]] = run;
+    }
+    run += v[k];
   }
 }
 
@@ -826,15 +842,13 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->n_maps, s->d_slot_base,
                                         s->d_cap_mask, inv_r, s->resolution, s->max_probe,
                                         s->d_slots, s->d_pt_slot, s->d_status);
-  first_kernel<<<g, kThreads, 0, st>>>(n, s->d_point_off, s->n_maps, s->d_slots, s->d_pt_slot,
-                                       first);
   // voxel ids in order of first appearance (scan of the first flags), assigned
   // to the voxels in the scan's last pass
   int rc = VGICP_OK;
   {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    scan_tile_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(first, n, nullptr,
-                                                                 s->d_scan_tmp);
+    first_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(s->d_pt_slot, s->d_slots, n, first,
+                                                             s->d_scan_tmp);
     scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(s->d_scan_tmp, nb, s->d_num_voxels);
     scan_assign_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
         first, s->d_flag, n, s->d_scan_tmp, s->d_pt_slot, s->d_slots, s->d_vcount, s->d_vkeys);
@@ -864,14 +878,20 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   }
   morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kSortSmemElems,
                        st>>>(
-      s->d_chunks, s->d_vbase, s->d_vkeys, vrank, vorder);
-  rank_counts_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_vcount, gcount);
+      s->d_chunks, s->d_vbase, s->d_vkeys, s->d_vcount, vrank, vorder, gcount);
   VGICP_CUDA_TRY(cudaGetLastError());
-  rc = launch_exclusive_scan(gcount, s->d_goff, n, s->d_num_voxels, s->d_scan_tmp,
-                             s->d_num_valid, st);
-  if (rc != VGICP_OK) return rc;
-  list_base_kernel<<<gv, kThreads, 0, st>>>(n, s->d_num_voxels, vrank, s->d_goff,
-                                            s->d_vslot_of);
+  // list offsets in rank order, and by voxel
+  {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    scan_tile_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(gcount, n, s->d_num_voxels,
+                                                                 s->d_scan_tmp);
+    scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(s->d_scan_tmp, nb, s->d_num_valid);
+    scan_lists_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(gcount, s->d_goff, n,
+                                                             s->d_num_voxels, s->d_scan_tmp,
+                                                             vorder, s->d_vslot_of);
+    VGICP_CUDA_TRY(cudaGetLastError());
+    count_launches(3);
+  }
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
   scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of,
                                          s->d_vcount, s->d_vfill, s->d_plist);
@@ -890,9 +910,9 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
       s->d_gpts, s->d_gcovs, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
       s->max_probe, s->d_vslots, s->d_lslot_of, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, first, vbase, sort, rank counts, list bases, scatter, vslot init, finalize
-  // (+ reset or init: 1; the two scans: 3 each)
-  count_launches(9);
+  // insert, vbase, sort, scatter, vslot init, finalize (+ reset or init: 1; the two
+  // scans: 3 each)
+  count_launches(6);
   s->built = true;
   return VGICP_OK;
 }

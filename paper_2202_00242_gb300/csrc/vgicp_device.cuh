@@ -13,7 +13,7 @@ namespace vgicp {
 
 // Hash slot (16 B, 16-B aligned): packed key, then (vid, count).
 //   key   : kEmptyKey or a packed voxel key (< 2^63)
-//   vid   : during the build, the smallest point index (map-local) of the voxel;
+//   vid   : during the build, the smallest point index (in the batch) of the voxel;
 //           after it, the global voxel index
 //   count : number of points in the voxel
 struct __align__(16) Slot {
