@@ -119,9 +119,28 @@ int stage_poses(vgicp_plan* P, const double* poses, int b) {
   return VGICP_OK;
 }
 
+// Copies n 16-byte words from pinned host memory (addressable from the device)
+// to device memory.
+__global__ void copy_words_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src,
+                                  int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// The poses go to the device through a kernel that reads the pinned staging
+// buffer, not through a copy engine: a host-to-device copy queued there would
+// wait behind whatever large upload the caller has in flight (for instance the
+// next step's clouds on another stream).
 int upload_poses(vgicp_plan* P, int b, cudaStream_t st) {
-  VGICP_CUDA_TRY(cudaMemcpyAsync(P->d_pd, P->h_pd[b], sizeof(PairDesc) * P->n_pairs,
-                                 cudaMemcpyHostToDevice, st));
+  static_assert(sizeof(PairDesc) % 16 == 0, "PairDesc is a whole number of 16-B words");
+  const int64_t words = (int64_t)sizeof(PairDesc) / 16 * P->n_pairs;
+  const int grid = (int)std::min<int64_t>((words + 255) / 256, 1024);
+  copy_words_kernel<<<std::max(grid, 1), 256, 0, st>>>(reinterpret_cast<uint4*>(P->d_pd),
+                                                        reinterpret_cast<const uint4*>(P->h_pd[b]),
+                                                        words);
+  VGICP_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
   VGICP_CUDA_TRY(cudaEventRecord(P->uploaded[b], st));
   P->used[b] = true;
   return VGICP_OK;
