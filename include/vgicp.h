@@ -107,7 +107,9 @@ int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t*
  * vgicp_build_voxelmap()), in their original order.  No allocation and no
  * synchronization: each lookup table keeps the region of the first build (at
  * least 2 n slots), so clouds with more voxels run at a higher load factor,
- * never above 1/2. */
+ * never above 1/2.  A rebuild empties only the table slots the previous build's
+ * voxels occupy (recorded by that build), so successive builds of one batch
+ * must be ordered: issue them on one stream, or synchronize between them. */
 int vgicp_rebuild_voxelmaps(vgicp_map* const* maps, int32_t n_maps, const float* points,
                             const float* covs, vgicp_stream_t stream);
 
