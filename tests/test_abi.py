@@ -138,3 +138,32 @@ def test_host_checks_of_se3_and_admission(lib):
     assert sched(mb, 2, None, 0, pairs, 1, 300, 1, bop, ctypes.byref(nb)) == 0
     assert nb.value == 1 and bop[0] == 0
     assert sched(mb, 2, None, 0, pairs, 0, 300, 1, bop, ctypes.byref(nb)) == 0 and nb.value == 0
+
+
+def test_host_checks_of_plans(lib):
+    """Plan creation and use reject bad arguments before any device work."""
+    from paper_2202_00242_gb300 import _lib
+    err = lambda: lib.vgicp_last_error_string()  # noqa: E731
+    h = ctypes.c_void_p()
+    maps = (ctypes.c_void_p * 1)(ctypes.c_void_p(8))
+    srcs = (_lib.Cloud * 1)()
+    pairs = (ctypes.c_int32 * 2)(0, 0)
+    create = lib.vgicp_plan_create
+    assert create(maps, 1, srcs, 1, pairs, 1, None, None, None) == -1 and b"out" in err()
+    assert create(None, 1, srcs, 1, pairs, 1, None, None, ctypes.byref(h)) == -1
+    assert create(maps, 1, srcs, 1, pairs, 0, None, None, ctypes.byref(h)) == -1
+    assert b"empty" in err() and not h.value
+    for nb, tile, variant, msg in [(5, 0, 0, b"neighbours"), (1, 1024, 0, b"2048"),
+                                   (1, 0, 7, b"variant")]:
+        opts = _lib.LinOpts(nb, tile, 0, variant, None, None)
+        assert create(maps, 1, srcs, 1, pairs, 1, ctypes.byref(opts), None,
+                      ctypes.byref(h)) == -1
+        assert msg in err() and not h.value
+    opts = _lib.LinOpts(1, 0, 0, 0, ctypes.c_void_p(16), None)
+    assert create(maps, 1, srcs, 1, pairs, 1, ctypes.byref(opts), None, ctypes.byref(h)) == -1
+    assert b"single-factor" in err()
+    poses = (ctypes.c_double * 16)()
+    assert lib.vgicp_plan_execute(None, poses, None, None, None, None, None) == -1
+    assert lib.vgicp_plan_autotune(None, poses, None) == -1
+    assert lib.vgicp_plan_info(None, None, None, None, None) == -1
+    assert lib.vgicp_plan_destroy(None) == 0
