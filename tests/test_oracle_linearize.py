@@ -422,3 +422,44 @@ def test_overlap_rate_pins(oracle_lib):
     hits = sum(tuple(k) in mk for k in np.floor(q / 0.5).astype(np.int64))
     assert len(keys) > 1
     assert oracle.overlap(vm, src, T) == hits / 300
+
+
+def test_27_neighbour_reduces_to_one_voxel_when_voxels_are_isolated(oracle_lib):
+    """With occupied voxels at least two keys apart on some axis, the 3 x 3 x 3
+    block of a point in an occupied voxel holds that voxel alone: the
+    27-neighbour factor is the 1-neighbour factor."""
+    rng = np.random.default_rng(21)
+    r = 0.5
+    lattice = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(2), indexing="ij"),
+                       -1).reshape(-1, 3) * 3  # voxel keys three apart
+    keys = lattice[rng.integers(0, len(lattice), 400)]
+    tp = ((keys + rng.uniform(0.1, 0.9, size=(400, 3))) * r).astype(np.float32)
+    tc = oracle_lib.knn_covariances(tp).astype(np.float32)
+    src_keys = lattice[rng.integers(0, len(lattice), 150)]
+    sp = ((src_keys + rng.uniform(0.2, 0.8, size=(150, 3))) * r).astype(np.float32)
+    sc = oracle_lib.knn_covariances(sp).astype(np.float32)
+    T = synth.make_pose(synth.axis_angle_matrix([0, 1, 0], 0.01), [0.01, -0.01, 0.005])
+    vm = oracle_lib.build_voxelmap(tp, tc, r)
+    one = oracle_lib.linearize(vm, sp, sc, T, neighbours=1)
+    many = oracle_lib.linearize(vm, sp, sc, T, neighbours=27)
+    assert one.inliers == many.inliers == sp.shape[0]
+    np.testing.assert_allclose(many.H, one.H, rtol=1e-14, atol=1e-14 * np.abs(one.H).max())
+    np.testing.assert_allclose(many.b, one.b, rtol=1e-14, atol=1e-14 * np.abs(one.H).max())
+    np.testing.assert_allclose(many.err, one.err, rtol=1e-14)
+
+
+def test_factor_is_a_sum_over_source_points(oracle_lib):
+    """Eq. 2 sums per-point terms: the factor of a source cloud is the sum of the
+    factors of any split of it (a dropped or doubled point fails this)."""
+    tp, tc, sp, sc, T, r = _room_case(2000, 3000, seed=5)
+    vm = oracle_lib.build_voxelmap(tp, tc, r)
+    Tp = _perturbed(T, seed=3)
+    whole = oracle_lib.linearize(vm, sp, sc, Tp)
+    mask = np.random.default_rng(4).random(sp.shape[0]) < 0.4
+    a = oracle_lib.linearize(vm, sp[mask], sc[mask], Tp)
+    b = oracle_lib.linearize(vm, sp[~mask], sc[~mask], Tp)
+    assert whole.inliers == a.inliers + b.inliers and 0 < a.inliers < whole.inliers
+    scale = np.abs(whole.H).max()
+    np.testing.assert_allclose(whole.H, a.H + b.H, rtol=1e-12, atol=1e-12 * scale)
+    np.testing.assert_allclose(whole.b, a.b + b.b, rtol=1e-12, atol=1e-12 * scale)
+    np.testing.assert_allclose(whole.err, a.err + b.err, rtol=1e-12)
