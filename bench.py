@@ -53,6 +53,9 @@ def parse_args(argv=None):
                     help="maps: each submap's own (voxel-grouped) cloud is the source of its "
                          "factors; clouds: the caller's arrays as given")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parity-pairs", type=int, default=8,
+                    help="factors of the timed set checked against the FP64 oracle after "
+                         "the timed region (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle baseline sample")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -83,7 +86,9 @@ def init_dist(backend):
     rank, world, _ = rank_env()
     if world > 1 and not dist.is_initialized():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        os.environ.setdefault("MASTER_PORT", "29511")
+        if "MASTER_PORT" not in os.environ:
+            raise RuntimeError("WORLD_SIZE > 1 needs MASTER_PORT (launch with "
+                               "torch.distributed.run, or pass --gpus N alone)")
         dist.init_process_group(backend=backend, rank=rank, world_size=world)
     return rank, world
 
@@ -236,6 +241,75 @@ def oracle_sample(w, budget_s, nthreads, start_pair=0, min_pairs=2):
         if done >= min_pairs and time.perf_counter() - t0 >= budget_s:
             break
     return pts_done, time.perf_counter() - t0, done
+
+
+# ---------------------------------------------------------------------------
+# parity of the measured results against the FP64 oracle (outside the timed region)
+# ---------------------------------------------------------------------------
+
+TOL = 1e-4
+
+
+def near_face_points(points, T, r, tol=1e-5) -> int:
+    """Source points whose binary64 position T mu lies within tol of a voxel face."""
+    q = points.astype(np.float64) @ T[:3, :3].T + T[:3, 3]
+    f = q / r - np.floor(q / r)
+    return int((np.minimum(f, 1.0 - f).min(axis=1) * r < tol).sum())
+
+
+def oracle_parity(w, out, inliers, poses, n_sample, neighbours=1, seed=0, grad=None,
+                  planted=False):
+    """Error of sampled factors against the FP64 oracle: H relative Frobenius,
+    b plain relative and relative to max(|b|, sqrt(err |H|_F)), err relative,
+    inlier mismatches and near-face points.  ``out`` (P, 43) and ``inliers`` (P,)
+    are host arrays; with ``grad`` (P, 6) the gradient 2 J^T W d is checked
+    against the oracle's 2 b instead of H and b, and ``out`` holds err only.
+    ``planted``: the poses are the scenes' ground truth, where b nearly vanishes;
+    b is then held to 1e-4 of the Cauchy-Schwarz scale, otherwise to plain 1e-4."""
+    import oracle
+    oracle.build()
+    P = w.pairs.shape[0]
+    sel = np.sort(np.random.default_rng(seed).choice(P, min(n_sample, P), replace=False))
+    maps = {}
+    eH, eb, ebc, ee, mism, near = [], [], [], [], 0, 0
+    for p in sel:
+        j, i = (int(x) for x in w.pairs[p])
+        if j not in maps:
+            maps[j] = oracle.build_voxelmap(*w.clouds.cloud(j), w.resolution)
+        sp, sc = w.clouds.cloud(i)
+        ref = oracle.linearize(maps[j], sp, sc, poses[p], neighbours=neighbours, nthreads=0)
+        mism += int(int(inliers[p]) != ref.inliers)
+        near += near_face_points(sp, poses[p], w.resolution)
+        if grad is not None:
+            g = np.asarray(grad[p], np.float64)
+            eb.append(np.linalg.norm(g - 2 * ref.b) / max(np.linalg.norm(2 * ref.b), 1e-300))
+            scale = max(np.linalg.norm(ref.b), np.sqrt(max(ref.err, 0.0) * np.linalg.norm(ref.H)))
+            ebc.append(np.linalg.norm(g - 2 * ref.b) / max(2 * scale, 1e-300))
+            ee.append(abs(float(out[p]) - ref.err) / max(abs(ref.err), 1e-300))
+            continue
+        o = np.asarray(out[p], np.float64)
+        H, b, e = o[:36].reshape(6, 6), o[36:42], float(o[42])
+        eH.append(np.linalg.norm(H - ref.H) / max(np.linalg.norm(ref.H), 1e-300))
+        eb.append(np.linalg.norm(b - ref.b) / max(np.linalg.norm(ref.b), 1e-300))
+        scale = max(np.linalg.norm(ref.b), np.sqrt(max(ref.err, 0.0) * np.linalg.norm(ref.H)))
+        ebc.append(np.linalg.norm(b - ref.b) / max(scale, 1e-300))
+        ee.append(abs(e - ref.err) / max(abs(ref.err), 1e-300))
+    res = {"pairs_checked": int(len(sel)), "pairs_sampled_from": int(P),
+           "neighbours": int(neighbours), "reference": "FP64 CPU oracle"}
+    if grad is None:
+        res["max_rel_fro_H"] = float(max(eH))
+    key = "max_rel_grad_vs_2b" if grad is not None else "max_rel_b"
+    res[key] = float(max(eb))
+    res[key + "_cs_scale"] = float(max(ebc))
+    res["max_rel_err"] = float(max(ee))
+    res["inlier_mismatches"] = int(mism)
+    res["near_face_points"] = int(near)
+    res["tolerance"] = TOL
+    res["poses"] = "planted (b held to the Cauchy-Schwarz scale)" if planted else "perturbed"
+    bmax = max(ebc) if planted else max(eb)
+    res["within_tolerance"] = bool(mism == 0 and bmax <= TOL and max(ee) <= TOL
+                                   and (grad is not None or max(eH) <= TOL))
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -446,6 +520,14 @@ def run_ours(args):
     h2d = pts_h.numel() * 4 + covs_h.numel() * 4
     d2h = out_h.numel() * 8 + inl_h.numel() * 8
 
+    # parity of the timed factor set: one more step, sampled factors against the oracle
+    parity = None
+    if args.parity_pairs > 0:
+        step()
+        torch.cuda.synchronize()
+        parity = oracle_parity(w, out.cpu().numpy(), inl.cpu().numpy(), w.poses,
+                               args.parity_pairs, seed=rank)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -490,6 +572,7 @@ def run_ours(args):
                     "pipelining": "upload of step k+1 (copy stream, second buffer) overlaps "
                                   "step k"},
             "batched_vs_per_factor": comparison,
+            "parity": parity,
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -660,9 +743,28 @@ def run_workload(args):
     clocks.start()
     ms = _timed(torch, step, K, args.warmup)
     clk = clocks.stop()
+    launches = lib.vgicp_launch_count() - launches0
     if args.workload == "large":
         extra["admission_batches"] = int(state["r"][2])
-    launches = lib.vgicp_launch_count() - launches0
+
+    # parity of the timed workload's results against the FP64 oracle (untimed)
+    parity = None
+    if args.parity_pairs > 0:
+        if args.workload == "room":
+            api.linearize(vm, spd, scd, T, out=out, inliers=inl)
+            parity = oracle_parity(w, out.cpu().numpy()[None], inl.cpu().numpy()[None], w.poses,
+                                   1)
+        elif args.workload == "corridor":
+            res = plan.execute(w.poses)
+            parity = oracle_parity(w, res.out.cpu().numpy(), res.inliers.cpu().numpy(), w.poses,
+                                   args.parity_pairs, planted=True)
+        elif args.workload == "differentiable":
+            g, err, inl_d = api.evaluate_batched(maps, srcs, w.pairs, w.poses, mode=api.GRADIENT)
+            parity = oracle_parity(w, err.cpu().numpy(), inl_d.cpu().numpy(), w.poses,
+                                   args.parity_pairs, grad=g.cpu().numpy())
+        elif args.workload == "large":
+            parity = oracle_parity(w, state["r"][0], state["r"][1], w.poses,
+                                   min(args.parity_pairs, 4), neighbours=27)
     value = n_pts / (ms / 1e3)
     peaks = {}
     try:
@@ -680,13 +782,39 @@ def run_workload(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "whole step (36 B per source point over the step time)"},
-        "gpu_launches": int(launches), "clocks": clk,
+        "parity": parity, "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(args, argv) -> int:
+    """--gpus N without a launcher: start N ranks of this script, one per GPU, with
+    torch.distributed.run on this node (127.0.0.1, a free port).  Returns the
+    launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1",
+           "--nproc-per-node", str(args.gpus), "--master-addr", "127.0.0.1",
+           "--master-port", str(free_port()), os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
 def main(argv=None):
+    argv = list(sys.argv[1:] if argv is None else argv)
     args = parse_args(argv)
+    env_world = os.environ.get("WORLD_SIZE")
+    if env_world is None and args.gpus > 1:
+        rc = launch_ranks(args, argv)
+        if rc != 0:
+            raise SystemExit(rc)
+        return
+    if env_world is not None and int(env_world) != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} disagrees with WORLD_SIZE={env_world}")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "global":

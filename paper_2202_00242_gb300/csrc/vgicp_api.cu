@@ -420,6 +420,8 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   int item = opts && opts->tile > 0 ? opts->tile : 0;
@@ -651,7 +653,7 @@ constexpr int32_t kNoAllocMaxItems = 4096;  // work items per call (1 MiB of par
 static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxItems + 1) * kPartialStride];
 
 std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64] = {nullptr};
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  The array's name
 // in host code only stands for the symbol; the address must be asked for with
@@ -659,7 +661,8 @@ double* g_noalloc_ptr[64] = {nullptr};
 int noalloc_scratch(double** out) {
   int dev = 0;
   VGICP_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return set_error(VGICP_ERR_INVALID_ARG, "device index above 63");
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(VGICP_ERR_INVALID_ARG, "device index beyond the supported range");
   std::lock_guard<std::mutex> g(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;

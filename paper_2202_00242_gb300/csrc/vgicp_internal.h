@@ -12,6 +12,9 @@
 
 namespace vgicp {
 
+// Device indices the library keeps per-device state for (0 .. kMaxDevices-1).
+constexpr int kMaxDevices = 64;
+
 // ---- error reporting -------------------------------------------------------
 int set_error(int code, const std::string& msg);
 int check_cuda(cudaError_t e, const char* what);

@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "vgicp_device.cuh"
 #include "vgicp_internal.h"
@@ -1160,14 +1161,22 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
 
   } else {
-    static bool attr_set[64] = {false};
+    // the dynamic shared-memory limit is a per-device function attribute: set it
+    // once per device, under a lock (host threads may launch concurrently)
+    static std::mutex attr_mu;
+    static bool attr_set[kMaxDevices] = {false};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-      VGICP_CUDA_TRY(cudaFuncSetAttribute(tma::linearize_tma_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(tma::Smem)));
-      attr_set[dev] = true;
+    VGICP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+      return set_error(VGICP_ERR_INVALID_ARG, "device index beyond the supported range");
+    {
+      std::lock_guard<std::mutex> lock(attr_mu);
+      if (!attr_set[dev]) {
+        VGICP_CUDA_TRY(cudaFuncSetAttribute(tma::linearize_tma_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(tma::Smem)));
+        attr_set[dev] = true;
+      }
     }
     tma::linearize_tma_kernel<<<grid, tma::kThreads, sizeof(tma::Smem), st>>>(L);
   }

@@ -41,6 +41,13 @@ def rel_fro(a, ref):
     return float(np.linalg.norm(np.asarray(a, np.float64) - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
+def b_rel(b, b_ref):
+    """Plain relative error of b: |b - b_ref| / |b_ref|."""
+    b_ref = np.asarray(b_ref, dtype=np.float64)
+    return float(np.linalg.norm(np.asarray(b, np.float64) - b_ref)
+                 / max(np.linalg.norm(b_ref), 1e-300))
+
+
 def b_error(b, b_ref, err_ref, H_ref):
     """Error of b relative to max(|b_ref|, sqrt(err |H|_F)): b vanishes at the
     optimum, and by Cauchy-Schwarz |b| <= sqrt(err * tr H) bounds its scale."""

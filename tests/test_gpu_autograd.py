@@ -72,6 +72,7 @@ def test_evaluate_modes_match_oracle(small_set):
         assert int(inl[p]) == ref.inliers
         scale = max(np.linalg.norm(2 * ref.b), 2 * np.sqrt(ref.err * np.linalg.norm(ref.H)))
         assert np.linalg.norm(g2[p] - 2 * ref.b) <= 1e-4 * scale
+        assert np.linalg.norm(g2[p] - 2 * ref.b) <= 1e-4 * np.linalg.norm(2 * ref.b)
         assert np.linalg.norm(g3[p] - gex) <= 1e-4 * max(scale, np.linalg.norm(gex))
         for e in (err, err3, err1):
             assert abs(float(e[p]) - ref.err) <= 1e-4 * ref.err
@@ -115,6 +116,7 @@ def test_autograd_gauss_newton_gradient_is_2b(small_set):
         ref, _, _ = _ref(w, omaps, p, w.poses[p])
         scale = max(np.linalg.norm(2 * ref.b), 2 * np.sqrt(ref.err * np.linalg.norm(ref.H)))
         assert np.linalg.norm(xi.grad[p].numpy() - 2 * ref.b) <= 1e-4 * scale
+        assert np.linalg.norm(xi.grad[p].numpy() - 2 * ref.b) <= 1e-4 * np.linalg.norm(2 * ref.b)
 
 
 def test_gradient_descent_refinement_reduces_cost(small_set):

@@ -5,8 +5,11 @@ Bars (arXiv 2202.00242 Sec. III-A quantities):
     covariances: bit-exact with the binary64 definition rounded to float32;
   * per-point correspondences (voxel index) and keys of T mu: bit-exact; the
     number of points within 1e-5 m of a voxel face is reported;
-  * H: relative Frobenius error <= 1e-4; b: error <= 1e-4 relative to
-    max(|b|, sqrt(err |H|_F)); err: relative error <= 1e-4; inliers exact.
+  * H: relative Frobenius error <= 1e-4; err: relative error <= 1e-4; inliers
+    exact; b: plain relative error |b - b_ref| / |b_ref| <= 1e-4 at every pose
+    away from the scene's planted pose.  At the planted pose b nearly vanishes
+    (it is the gradient at the optimum), so there b is held to 1e-4 relative to
+    max(|b|, sqrt(err |H|_F)), the scale Cauchy-Schwarz bounds |b| by.
 """
 import numpy as np
 import pytest
@@ -36,14 +39,20 @@ def cu(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def check_factor(out, inl, ref, what=""):
+def check_factor(out, inl, ref, what="", planted=False):
+    """H, b, err and the inlier count of one factor against the oracle's.
+    ``planted``: the pose is the scene's planted (ground-truth) pose, where b is
+    held to the Cauchy-Schwarz scale only; elsewhere also to plain 1e-4."""
     H, b, err = api.unpack(out.cpu().double())
     H, b, err = H.numpy(), b.numpy(), float(err)
     assert int(inl) == ref.inliers, what
     eH = cases.rel_fro(H, ref.H)
     eb = cases.b_error(b, ref.b, ref.err, ref.H)
+    ebp = cases.b_rel(b, ref.b)
     ee = abs(err - ref.err) / max(abs(ref.err), 1e-300)
     assert eH <= TOL and eb <= TOL and ee <= TOL, (what, eH, eb, ee)
+    if not planted:
+        assert ebp <= TOL, (what, "plain relative b", ebp)
     assert np.array_equal(H, H.T)
     return eH, eb, ee
 
@@ -87,14 +96,15 @@ def test_linearize_room_matches_oracle(dev, which):
     ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, debug=True)
     assert np.array_equal(lin.qkeys.cpu().numpy().astype(np.int64), ref.qkeys)
     assert np.array_equal(lin.corr.cpu().numpy().astype(np.int64), ref.corr)
-    check_factor(lin.out, lin.inliers, ref, which)
+    check_factor(lin.out, lin.inliers, ref, which, planted=which == "planted")
     print(f"near-face points (<1e-5 m): {cases.near_face_count(sp, T, r)} of {sp.shape[0]}")
 
 
 @pytest.mark.parametrize("n", [1, 31, 255, 256, 257, 1000, 8191])
 @pytest.mark.parametrize("tile", [256, 1024, 0])
 def test_ragged_sizes_and_tiles(dev, n, tile):
-    tp, tc, sp, sc, T, r = cases.room()
+    tp, tc, sp, sc, T_true, r = cases.room()
+    T = synth.perturb_pose(np.random.default_rng(3), T_true, 0.05, 1.0)
     vm = api.VoxelMap.build(cu(tp), cu(tc), r)
     lin = api.linearize(vm, cu(sp[:n]), cu(sc[:n]), T, tile=tile)
     ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp[:n], sc[:n], T)
@@ -171,9 +181,12 @@ def test_outdoor_submaps_batched(dev):
         check_factor(bat.out[p], bat.inliers[p], ref, f"pair {p}")
 
 
+@pytest.mark.parametrize("pose", ["planted", "perturbed"])
 @pytest.mark.parametrize("mode", ["single", "batched"])
-def test_27_neighbours_match_oracle(dev, mode):
+def test_27_neighbours_match_oracle(dev, mode, pose):
     tp, tc, sp, sc, T, r = cases.room(seed=4, n_target=4096, n_source=3000)
+    if pose == "perturbed":
+        T = synth.perturb_pose(np.random.default_rng(4), T, 0.05, 1.0)
     vm = api.VoxelMap.build(cu(tp), cu(tc), r)
     ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, neighbours=27,
                            debug=True)
@@ -185,7 +198,7 @@ def test_27_neighbours_match_oracle(dev, mode):
         bat = api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 0]], T[None], neighbours=27,
                                     tile=512)
         out, inl = bat.out[0], bat.inliers[0]
-    check_factor(out, inl, ref, mode)
+    check_factor(out, inl, ref, mode, planted=pose == "planted")
 
 
 def test_repeated_linearizations_identical(dev):
@@ -248,7 +261,7 @@ def test_build_error_paths_leave_context_usable(dev):
     vm.status()
     lin = api.linearize(vm, cu(sp), cu(sc), T)
     ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T)
-    check_factor(lin.out, lin.inliers, ref)
+    check_factor(lin.out, lin.inliers, ref, planted=True)
 
 
 def test_pose_validation(dev):
@@ -267,17 +280,21 @@ def test_pose_validation(dev):
         api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 1]], T[None])
 
 
+@pytest.mark.parametrize("pose", ["planted", "perturbed"])
 @pytest.mark.parametrize("variant", [1, 2, 3])
-def test_kernel_variants_match_oracle(dev, variant):
+def test_kernel_variants_match_oracle(dev, variant, pose):
     tp, tc, sp, sc, T, r = cases.room()
+    if pose == "perturbed":
+        T = synth.perturb_pose(np.random.default_rng(6), T, 0.05, 1.0)
     vm = api.VoxelMap.build(cu(tp), cu(tc), r)
     lin = api.linearize(vm, cu(sp), cu(sc), T, corr=True, variant=variant)
     ref = oracle.linearize(oracle.build_voxelmap(tp, tc, r), sp, sc, T, debug=True)
     assert np.array_equal(lin.corr.cpu().numpy().astype(np.int64), ref.corr)
-    check_factor(lin.out, lin.inliers, ref, f"variant {variant}")
+    planted = pose == "planted"
+    check_factor(lin.out, lin.inliers, ref, f"variant {variant}", planted=planted)
     bat = api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 0]], T[None], variant=variant,
                                 tile=1000)
-    check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}")
+    check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}", planted=planted)
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])

@@ -56,8 +56,8 @@ def _reference_worker(rank, world, port, q):
     import bench
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
-        bench.main(["--impl", "reference", "--submaps", "3", "--neighbours-per-submap", "1",
-                    "--steps", "1", "--warmup", "3"])
+        bench.main(["--gpus", str(world), "--impl", "reference", "--submaps", "3",
+                    "--neighbours-per-submap", "1", "--steps", "1", "--warmup", "3"])
     q.put((rank, buf.getvalue()))
 
 
@@ -78,3 +78,32 @@ def test_reference_arm_prints_on_rank_zero_only():
     line = json.loads(res[0].strip())
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.timeout(300)
+def test_gpus_flag_starts_one_rank_per_gpu():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself
+    (torch.distributed.run on 127.0.0.1, a free port); the reference arm then
+    runs on rank 0 only and reports the world size."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2",
+                        "--impl", "reference", "--submaps", "3", "--neighbours-per-submap", "1",
+                        "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, env=env, timeout=280)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+
+
+def test_gpus_flag_must_match_launcher_world_size(monkeypatch):
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    with pytest.raises(SystemExit):
+        bench.main(["--gpus", "3", "--impl", "reference"])
