@@ -696,15 +696,18 @@ def run_workload(args):
         maps = api.build_voxelmaps(pts, covs, off, w.resolution)
         srcs = [(pts[off[c]:off[c + 1]], covs[off[c]:off[c + 1]]) for c in range(C)]
         fs = autograd.FactorSet(maps, srcs, w.pairs, w.poses)
-        xi = torch.zeros((w.pairs.shape[0], 6), dtype=torch.float64, requires_grad=True)
+        xi = torch.zeros((w.pairs.shape[0], 6), dtype=torch.float64, device=dev,
+                         requires_grad=True)
 
         def step():
             xi.grad = None
             fs.cost(xi).sum().backward()
         n_pts = int(w.source_points_per_step)
         name = f"differentiable_{w.pairs.shape[0]}pairs_20k-50k_r{w.resolution:g}"
-        extra["step"] = ("forward (cost kernel) + backward (gradient kernel, J_r^T on the host) "
-                         "of the autograd Function over all factors; points counted once")
+        extra["step"] = ("forward (poses T0 Exp(xi) composed on the device, cost kernel) + "
+                         "backward (gradient kernel, J_r^T and the incoming gradient applied "
+                         "on the device) of the autograd Function over all factors, xi on the "
+                         "GPU; points counted once")
     elif args.workload == "covariances":
         w = synth.config_global_map(n_submaps=args.submaps)
         pts = torch.from_numpy(w.clouds.points).to(dev)
@@ -746,6 +749,16 @@ def run_workload(args):
     launches = lib.vgicp_launch_count() - launches0
     if args.workload == "large":
         extra["admission_batches"] = int(state["r"][2])
+    if args.workload == "differentiable":
+        # device time of the two evaluations one autograd step launches (cost,
+        # then gradient with J_r^T and the incoming gradient), back to back
+        x0 = torch.zeros((w.pairs.shape[0], 6), dtype=torch.float64, device=dev)
+        ones = torch.ones(w.pairs.shape[0], dtype=torch.float64, device=dev)
+
+        def two_evaluations():
+            fs.plan.evaluate(fs.base, x0, mode=api.COST)
+            fs.plan.evaluate(fs.base, x0, mode=api.GRADIENT, grad_scale=ones)
+        extra["device_ms_cost_plus_gradient"] = _timed(torch, two_evaluations, K, args.warmup)
 
     # parity of the timed workload's results against the FP64 oracle (untimed)
     parity = None

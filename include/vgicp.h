@@ -64,6 +64,24 @@ int vgicp_version(void);
  * (all threads, all devices); for accounting in benchmarks. */
 int64_t vgicp_launch_count(void);
 
+/* Fault injection for tests of error handling (no counterpart in the paper):
+ * the next `count` device allocations the library would make fail with
+ * VGICP_ERR_OOM, without calling the allocator, exactly as a real out-of-memory
+ * would; count = 0 cancels.  Applies to all threads and devices.  A negative
+ * count is VGICP_ERR_INVALID_ARG. */
+int vgicp_test_fail_allocations(int32_t count);
+
+/* Fault injection for tests of the staged kernel's bounded waits (no
+ * counterpart in the paper).  Arms the next launch of the staged kernel
+ * (variant 2) only: in every CTA the producer withholds its tile number `tile`
+ * (0-based; neither its copies nor its arrivals are issued), and every mbarrier
+ * wait of that launch gives up after limit_ns (0 < limit_ns <= 2e9) instead of
+ * 2 s.  The consumers' wait for the withheld tile then runs out, the launch
+ * sets its status word (that call's outputs become NaN, inliers -1), each
+ * producer waits for its copies in flight, and the kernel returns; the context
+ * stays usable.  A CTA with fewer tiles withholds nothing. */
+int vgicp_test_expire_waits(int32_t tile, int64_t limit_ns);
+
 /* ------------------------------------------------------------------------ */
 /* Voxel maps (Sec. III-A: the target cloud P_j is split into voxels, and each
  * voxel keeps one Gaussian formed from the means and covariances of the points
@@ -144,7 +162,10 @@ typedef struct {
   int32_t variant;    /* 1-neighbour kernel: 0 = automatic, 1 = one point per thread,
                          2 = shared-memory staged (bulk asynchronous copies),
                          3 = per-warp hit compaction (terms evaluated in full
-                             warps from a shared-memory queue) */
+                             warps from a shared-memory queue),
+                         4 = point pairs (two points per thread, packed float32x2
+                             arithmetic); the debug outputs corr_out / qkey_out
+                             always use kernel 1 */
   int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
                          point's own voxel (first-appearance numbering) or -1 */
   int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
@@ -336,7 +357,7 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
                       int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                       const vgicp_lin_opts* opts, vgicp_stream_t stream, vgicp_plan** out);
 
-/* Synchronizes.  Times each kernel variant (1-neighbour: 1, 2, 3) with work items
+/* Synchronizes.  Times each kernel variant (1-neighbour: 1 to 4) with work items
  * of 4096, 8192, 16384 and 32768 points on these poses (host, n_pairs x 16) and
  * keeps the fastest; results then depend (within float32 rounding) on that
  * choice, and are deterministic for it. */
@@ -350,6 +371,29 @@ int vgicp_plan_autotune(vgicp_plan* plan, const double* poses, vgicp_stream_t st
  * graph. */
 int vgicp_plan_execute(vgicp_plan* plan, const double* poses, double* out, int64_t* inliers,
                        void* kernel_start, void* kernel_stop, vgicp_stream_t stream);
+
+/* Differentiable evaluation (Sec. III-A: the matching cost as a function of the
+ * pose, differentiated for a gradient-based optimizer).  Every factor p is
+ * evaluated at T_p = T0_p Exp(xi_p), composed on the device in binary64, with
+ * the one-point-per-thread kernel and the plan's work list; nothing is copied
+ * to or from the host and the call does not synchronize.
+ *   base_poses: device, n_pairs x 16 doubles (row-major T0_p, finite rigid).
+ *   xi:         device, n_pairs x 6 doubles ([omega; v]), or NULL for xi = 0.
+ *   mode 1: err only; 2: gradient with W held, 2 J^T W d; 3: exact gradient
+ *           (adds the change of W with the rotation); see vgicp_evaluate_batched.
+ *   grad_scale: device, n_pairs doubles, or NULL (= 1): the gradient of factor p
+ *           is multiplied by grad_scale[p] (the incoming gradient of a
+ *           reverse-mode pass).
+ *   out: device, n_pairs x 7 doubles: [0..5] the gradient with respect to xi_p,
+ *        J_r(xi_p)^T g (modes 2, 3; g when xi is NULL), times grad_scale; [6] err.
+ *   inliers: device n_pairs, or NULL.
+ * A base pose that is not a finite rigid transform, or a non-finite xi, makes
+ * every output of the call NaN (inliers -1).  Calls on one plan, including
+ * vgicp_plan_execute, must be ordered on one stream: they share the plan's
+ * pose descriptors. */
+int vgicp_plan_evaluate(vgicp_plan* plan, const double* base_poses, const double* xi,
+                        int32_t mode, const double* grad_scale, double* out, int64_t* inliers,
+                        vgicp_stream_t stream);
 
 /* Current launch shape: kernel variant, points per work item, CTAs, work items. */
 int vgicp_plan_info(const vgicp_plan* plan, int32_t* variant, int32_t* item_points,

@@ -34,6 +34,8 @@ SIGNATURES = {
     "vgicp_last_error_string": (ctypes.c_char_p, []),
     "vgicp_version": (ctypes.c_int, []),
     "vgicp_launch_count": (i64, []),
+    "vgicp_test_fail_allocations": (ctypes.c_int, [i32]),
+    "vgicp_test_expire_waits": (ctypes.c_int, [i32, i64]),
     "vgicp_build_voxelmap": (ctypes.c_int, [P, P, i64, f64, ctypes.POINTER(MapOpts), P,
                                             ctypes.POINTER(P)]),
     "vgicp_build_voxelmaps": (ctypes.c_int, [P, P, P, i32, f64, ctypes.POINTER(MapOpts), P,
@@ -65,6 +67,7 @@ SIGNATURES = {
                                          i64, ctypes.POINTER(LinOpts), P, ctypes.POINTER(P)]),
     "vgicp_plan_autotune": (ctypes.c_int, [P, P, P]),
     "vgicp_plan_execute": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "vgicp_plan_evaluate": (ctypes.c_int, [P, P, P, i32, P, P, P, P]),
     "vgicp_plan_info": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32), ctypes.POINTER(i64)]),
     "vgicp_plan_destroy": (ctypes.c_int, [P]),

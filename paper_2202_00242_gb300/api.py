@@ -283,6 +283,30 @@ class Plan:
                                            _stream_ptr(stream)))
         return Linearization(out, inliers)
 
+    def evaluate(self, base_poses: torch.Tensor, xi: torch.Tensor | None = None, mode=2,
+                 grad_scale: torch.Tensor | None = None, out=None, inliers=None, stream=None):
+        """Cost (mode 1) or gradient (2: W held, 3: exact) of every factor at
+        T_p = base_p Exp(xi_p), composed on the device.  base_poses: CUDA float64
+        (P, 4, 4); xi: CUDA float64 (P, 6) or None; grad_scale: CUDA float64 (P,)
+        or None.  Returns (out (P, 7): gradient w.r.t. xi (6) and err, inliers)."""
+        P = self.n_pairs
+        for name, t, shape in (("base_poses", base_poses, (P, 4, 4)), ("xi", xi, (P, 6)),
+                               ("grad_scale", grad_scale, (P,))):
+            if t is None:
+                continue
+            if not t.is_cuda or t.dtype != torch.float64 or tuple(t.shape) != shape \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor {shape}")
+        if out is None:
+            out = torch.empty((P, 7), dtype=torch.float64, device=self.device)
+        if inliers is None:
+            inliers = torch.empty(P, dtype=torch.int64, device=self.device)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        check(self._lib.vgicp_plan_evaluate(self._h, ptr(base_poses), ptr(xi), int(mode),
+                                            ptr(grad_scale), ptr(out), ptr(inliers),
+                                            _stream_ptr(stream)))
+        return out, inliers
+
     def info(self) -> dict:
         v, it, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         n = ctypes.c_int64()

@@ -13,6 +13,7 @@
 
 #include "vgicp.h"
 #include "vgicp_internal.h"
+#include "vgicp_se3.cuh"
 
 namespace vgicp {
 
@@ -29,41 +30,10 @@ uint32_t next_pow2(uint64_t x) {
 
 }  // namespace
 
-bool finite_pose(const double* T) {
-  for (int i = 0; i < 16; ++i)
-    if (!std::isfinite(T[i])) return false;
-  if (T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0) return false;
-  // R^T R = I and det R = +1 within float32-level tolerance
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < 3; ++k) s += T[4 * k + i] * T[4 * k + j];
-      if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 1e-5) return false;
-    }
-  double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
-               T[2] * (T[4] * T[9] - T[5] * T[8]);
-  return det > 0.0;
-}
+bool finite_pose(const double* T) { return se3::rigid(T); }
 
 PairDesc make_pair_desc(const double* T, int32_t map, int32_t src) {
-  PairDesc p;
-  std::memset(&p, 0, sizeof(p));
-  double tmax = 0.0;
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) {
-      p.R[3 * i + j] = (float)T[4 * i + j];
-      p.R64[3 * i + j] = T[4 * i + j];
-    }
-    p.t[i] = (float)T[4 * i + 3];
-    p.t64[i] = T[4 * i + 3];
-    tmax = std::max(tmax, std::fabs(T[4 * i + 3]));
-  }
-  float tm = (float)tmax;
-  if ((double)tm < tmax) tm = std::nextafter(tm, INFINITY);
-  p.tmax = tm;
-  p.map = map;
-  p.src = src;
-  return p;
+  return se3::pair_desc(T, map, src);
 }
 
 MapDesc make_map_desc(const vgicp_map* m) {
@@ -170,7 +140,7 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   const size_t o_gpts = take(sizeof(float) * 3 * n);
   const size_t o_gcovs = take(sizeof(float) * 6 * n);
   const size_t o_scan = take(sizeof(uint32_t) * s->scan_tmp_elems);
-  cudaError_t e = cudaMalloc(&s->d_block, off);
+  cudaError_t e = device_malloc(&s->d_block, off, nullptr, false);
   if (e != cudaSuccess) {
     delete s;
     cudaGetLastError();
@@ -249,7 +219,25 @@ int set_error(int code, const std::string& msg) {
 
 int check_cuda(cudaError_t e, const char* what) {
   g_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // not sticky: clear it so the context stays usable
+    return VGICP_ERR_OOM;
+  }
   return VGICP_ERR_CUDA;
+}
+
+// Allocations the test hook makes fail (vgicp_test_fail_allocations).
+std::atomic<int32_t> g_fail_allocs{0};
+
+cudaError_t device_malloc(void** p, size_t bytes, cudaStream_t st, bool stream_ordered) {
+  int32_t k = g_fail_allocs.load(std::memory_order_relaxed);
+  while (k > 0) {
+    if (g_fail_allocs.compare_exchange_weak(k, k - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return stream_ordered ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
 }
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -279,6 +267,17 @@ const char* vgicp_last_error_string(void) { return g_error.c_str(); }
 int vgicp_version(void) { return 10000; }
 
 int64_t vgicp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int vgicp_test_fail_allocations(int32_t count) {
+  if (count < 0) return set_error(VGICP_ERR_INVALID_ARG, "negative count");
+  g_fail_allocs.store(count, std::memory_order_relaxed);
+  return VGICP_OK;
+}
+
+int vgicp_test_expire_waits(int32_t tile, int64_t limit_ns) {
+  g_error.clear();
+  return arm_wait_test(tile, limit_ns);
+}
 
 int vgicp_build_voxelmaps(const float* points, const float* covs, const int64_t* offsets,
                           int32_t n_maps, double resolution, const vgicp_map_opts* opts,
@@ -453,7 +452,7 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   // scratch: partials (n_items x 32 doubles) followed by the status word
   char* scratch = nullptr;
   const size_t part_bytes = sizeof(double) * kPartialStride * std::max<int32_t>(n_items, 1);
-  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch), part_bytes + 256, st));
+  VGICP_CUDA_TRY(device_malloc(reinterpret_cast<void**>(&scratch), part_bytes + 256, st, true));
   L.partials = reinterpret_cast<double*>(scratch);
   L.status = reinterpret_cast<int32_t*>(scratch + part_bytes);
   cudaError_t e = cudaMemsetAsync(L.status, 0, 2 * sizeof(int32_t), st);
@@ -594,7 +593,7 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* dev = nullptr;
-  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dev), off, st));
+  VGICP_CUDA_TRY(device_malloc(reinterpret_cast<void**>(&dev), off, st, true));
   int rc = VGICP_OK;
   // (a copy from pageable memory returns once the source has been staged, so
   // `host` may be released when this function returns)

@@ -787,7 +787,7 @@ int size_lookup_tables(MapSet* s, cudaStream_t st) {
   s->vslot_base[s->n_maps] = total;
   if (total >= (int64_t)0xFFFFFFFFll)
     return set_error(VGICP_ERR_INVALID_ARG, "more than 2^32-1 lookup slots in one batch");
-  cudaError_t e = cudaMalloc(&s->d_vblock, sizeof(VSlot) * (size_t)total);
+  cudaError_t e = device_malloc(&s->d_vblock, sizeof(VSlot) * (size_t)total, nullptr, false);
   if (e != cudaSuccess) {
     cudaGetLastError();
     s->d_vblock = nullptr;

@@ -298,7 +298,7 @@ int vgicp_downsample(const float* points, const float* times, const int64_t* off
   const size_t o_scan = take(sizeof(uint32_t) * scan_tmp_elems(n));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* d = nullptr;
-  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d), off, st));
+  VGICP_CUDA_TRY(device_malloc(reinterpret_cast<void**>(&d), off, st, true));
   auto U = [&](size_t o) { return reinterpret_cast<uint32_t*>(d + o); };
   int64_t* d_off = reinterpret_cast<int64_t*>(d + o_off);
   int64_t* d_base = reinterpret_cast<int64_t*>(d + o_base);

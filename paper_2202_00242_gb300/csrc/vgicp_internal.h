@@ -17,7 +17,10 @@ constexpr int kMaxDevices = 64;
 
 // ---- error reporting -------------------------------------------------------
 int set_error(int code, const std::string& msg);
-int check_cuda(cudaError_t e, const char* what);
+int check_cuda(cudaError_t e, const char* what);  // cudaErrorMemoryAllocation -> OOM
+// Every device allocation of the library (cudaMalloc, or cudaMallocAsync on st
+// when stream_ordered); fails without allocating while the test hook asks.
+cudaError_t device_malloc(void** p, size_t bytes, cudaStream_t st, bool stream_ordered);
 #define VGICP_CUDA_TRY(call)                                   \
   do {                                                         \
     cudaError_t e__ = (call);                                  \
@@ -125,8 +128,15 @@ struct LinLaunch {
   int32_t grid;              // 0 = automatic
   cudaEvent_t ev_start;      // optional, recorded around the kernel
   cudaEvent_t ev_stop;
+  int64_t wait_limit_ns;     // staged kernel: bound of its mbarrier waits (0 = 2 s)
+  int32_t test_withhold_tile;  // staged kernel, tests only: 1 + the tile index each
+                               // producer withholds (0 = none)
 };
 int launch_linearize(const LinLaunch& L, cudaStream_t st);
+
+// Arms the one-shot wait test of the next staged-kernel launch
+// (vgicp_test_expire_waits).
+int arm_wait_test(int32_t tile, int64_t limit_ns);
 
 // Points per work item and the persistent grid the linearize kernel uses.
 int default_item_size();
@@ -136,9 +146,12 @@ int default_variant();
 // Sum each pair's partials over its items [span[p].x, span[p].y) in order and
 // expand to the 43-double result; span == nullptr means one pair over all
 // n_items_single items.  A nonzero *status turns every output into NaN.
+// Gradient modes: jr (n_pairs x 36, device, or null) gives J_r^T g instead of g,
+// gscale (n_pairs, device, or null) scales the gradient.
 int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
                   int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
-                  cudaStream_t st, int32_t mode = 0);
+                  cudaStream_t st, int32_t mode = 0, const double* jr = nullptr,
+                  const double* gscale = nullptr);
 
 int device_sm_count();
 

@@ -556,7 +556,7 @@ int vgicp_estimate_covariances(const float* points, const int64_t* offsets, int3
   const size_t o_members = take(sizeof(float4) * n);
   const size_t o_scan = take(sizeof(uint32_t) * scan_tmp_elems(cap_total));
   char* d = nullptr;
-  VGICP_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d), off, st));
+  VGICP_CUDA_TRY(device_malloc(reinterpret_cast<void**>(&d), off, st, true));
   auto P = [&](size_t o) { return d + o; };
   int64_t* d_off = reinterpret_cast<int64_t*>(P(o_off));
   int64_t* d_base = reinterpret_cast<int64_t*>(P(o_base));

@@ -301,13 +301,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: gives up after 2 s (a bug, never a normal state).
+// Bounded wait: gives up after limit_ns (2 s by default: a bug, never a normal
+// state; a test launch may set a shorter limit).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 // L2 policies: the source stream is read once per factor (evict first), while
@@ -441,21 +443,28 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
   }
   __syncthreads();
 
+  const uint64_t wait_ns = L.wait_limit_ns > 0 ? (uint64_t)L.wait_limit_ns : kWaitLimitNs;
   if (warp == kNCW) {
     // ---------------- producer ----------------
     if (lane != 0) return;
     const uint64_t stream_pol = policy_evict_first();
     uint32_t u = 0;  // tiles issued
-    bool ok = true;
-    for (int it = blockIdx.x; it < L.n_items && ok; it += gridDim.x) {
+    bool ok = true, withheld = false;
+    for (int it = blockIdx.x; it < L.n_items && ok && !withheld; it += gridDim.x) {
       int pair, b, e;
       item_bounds(L, it, pair, b, e);
       const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
       const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
       for (int t0 = b; t0 < e; t0 += kTile) {
         const int s = u % kStages;
-        if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1)) {
+        if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1, wait_ns)) {
           ok = false;
+          break;
+        }
+        if (L.test_withhold_tile > 0 && u + 1 == (uint32_t)L.test_withhold_tile) {
+          // test launch: this tile is never issued (no copy, no arrival), so the
+          // consumers' bounded wait for it runs out
+          withheld = true;
           break;
         }
         const int n = min(kTile, e - t0);
@@ -482,9 +491,9 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
         ++u;
       }
     }
-    if (ok) {
+    if (ok && !withheld) {
       const int s = u % kStages;
-      if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1)) ok = false;
+      if (u >= kStages && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1, wait_ns)) ok = false;
       if (ok) {
         S.desc[s].n = -1;
         mbar_arrive(&S.full[s]);
@@ -492,11 +501,11 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
         ++u;
       }
     }
-    if (!ok) {
-      atomicExch(L.status, 1);
+    if (!ok) atomicExch(L.status, 1);
+    if (!ok || withheld) {
       // let copies already in flight land before the block exits
       for (uint32_t v = (u > kStages ? u - kStages : 0); v < u; ++v)
-        mbar_wait(&S.full[v % kStages], (v / kStages) & 1);
+        mbar_wait(&S.full[v % kStages], (v / kStages) & 1, wait_ns);
     }
     return;
   }
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
 
   for (uint32_t u = 0;; ++u) {
     const int s = u % kStages;
-    if (!mbar_wait(&S.full[s], (u / kStages) & 1)) {
+    if (!mbar_wait(&S.full[s], (u / kStages) & 1, wait_ns)) {
       atomicExch(L.status, 1);
       break;
     }
@@ -1285,8 +1294,14 @@ __global__ void __launch_bounds__(kThreads, VGICP_PAIR_MIN_BLOCKS)
     for (int k = 0; k < kTerms; ++k) acc[k] = make_float2(0.0f, 0.0f);
     int hits = 0;
 
-    for (int p = begin + threadIdx.x; p < end; p += kStride) {
-      const int pb = p + kThreads;
+    // The loop bound is the same for the 32 lanes of a warp (p0 is the warp's
+    // first point), so every lane reaches the warp vote below; a lane whose
+    // point lies past the end reads the item's first point and is masked.
+    for (int p0 = begin + (threadIdx.x & ~31); p0 < end; p0 += kStride) {
+      const int pr = p0 + lane;
+      const bool has_a = pr < end;
+      const int p = has_a ? pr : begin;
+      const int pb = pr + kThreads;
       const bool has_b = pb < end;
       const int pq = has_b ? pb : p;  // past the end: re-read p, masked below
       const float4 g3 = lds_f4(&ic.tmax);
@@ -1332,7 +1347,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_PAIR_MIN_BLOCKS)
       uint32_t ha, hb;
       unsigned long long keya, keyb;
       uint32_t sa[8], sb[8], ta[8], tb[8];
-      const bool la = probe_first(vs, mask, kxa, kya, kza, pol, ha, keya, sa, sb);
+      const bool la = probe_first(vs, mask, kxa, kya, kza, pol, ha, keya, sa, sb) && has_a;
       const bool lb = probe_first(vs, mask, kxb, kyb, kzb, pol, hb, keyb, ta, tb) && has_b;
       const int max_probe = ic.max_probe;
       const bool hit_a = probe_rest(vs, mask, max_probe, la, ha, keya, pol, sa, sb);
@@ -1384,11 +1399,16 @@ __global__ void __launch_bounds__(kThreads, VGICP_PAIR_MIN_BLOCKS)
 }
 }  // namespace pairk
 
-// One warp per pair: lane k sums term k over the pair's items in order.
+// One warp per pair: lane k sums term k over the pair's items in order.  For the
+// gradient modes, an optional right Jacobian per pair (jr, 36 doubles, row-major)
+// maps the gradient g of the right perturbation to that of the pose increment,
+// J_r^T g, and an optional per-pair scale multiplies it (the incoming gradient of
+// a reverse-mode pass).
 __global__ void reduce_kernel(const double* __restrict__ partials, const int2* __restrict__ span,
                               int32_t n_items_single, int64_t n_pairs,
                               const int32_t* __restrict__ status, double* __restrict__ out,
-                              int64_t* __restrict__ inliers, int32_t mode) {
+                              int64_t* __restrict__ inliers, int32_t mode,
+                              const double* __restrict__ jr, const double* __restrict__ gscale) {
   const int64_t pair = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
@@ -1403,6 +1423,20 @@ __global__ void reduce_kernel(const double* __restrict__ partials, const int2* _
     return;
   }
   if (mode != 0) {  // gradient (6) and err (1)
+    if (jr && mode >= 2) {
+      double g[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) g[i] = __shfl_sync(0xFFFFFFFFu, s, i);
+      if (lane < 6) {
+        const double* J = jr + pair * 36;
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v = fma(J[6 * i + lane], g[i], v);
+        s = gscale ? v * gscale[pair] : v;
+      }
+    } else if (gscale && lane < 6 && mode >= 2) {
+      s *= gscale[pair];
+    }
     if (lane < 7) out[pair * 7 + lane] = s;
     if (lane == 28) inliers[pair] = (status && *status != 0) ? -1 : (int64_t)llrint(s);
     return;
@@ -1430,6 +1464,32 @@ __global__ void reduce_kernel(const double* __restrict__ partials, const int2* _
 }
 
 }  // namespace
+
+// One-shot test state for the staged kernel's bounded waits
+// (vgicp_test_expire_waits): the tile its producers withhold (+1; 0 = none) and
+// the wait limit of that one launch.
+std::mutex g_wait_test_mu;
+int32_t g_wait_test_tile = 0;
+int64_t g_wait_test_ns = 0;
+
+void take_wait_test(LinLaunch& L) {
+  std::lock_guard<std::mutex> lock(g_wait_test_mu);
+  if (g_wait_test_tile > 0) {
+    L.test_withhold_tile = g_wait_test_tile;
+    L.wait_limit_ns = g_wait_test_ns;
+    g_wait_test_tile = 0;
+    g_wait_test_ns = 0;
+  }
+}
+
+int arm_wait_test(int32_t tile, int64_t limit_ns) {
+  if (tile < 0 || limit_ns <= 0 || limit_ns > 2000000000ll)
+    return set_error(VGICP_ERR_INVALID_ARG, "tile must be >= 0 and the limit in (0, 2 s]");
+  std::lock_guard<std::mutex> lock(g_wait_test_mu);
+  g_wait_test_tile = tile + 1;
+  g_wait_test_ns = limit_ns;
+  return VGICP_OK;
+}
 
 int default_item_size() { return 16384; }
 
@@ -1492,7 +1552,9 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
         attr_set[dev] = true;
       }
     }
-    tma::linearize_tma_kernel<<<grid, tma::kThreads, sizeof(tma::Smem), st>>>(L);
+    LinLaunch Lt = L;
+    take_wait_test(Lt);
+    tma::linearize_tma_kernel<<<grid, tma::kThreads, sizeof(tma::Smem), st>>>(Lt);
   }
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(1);
@@ -1502,12 +1564,12 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
 
 int launch_reduce(const double* partials, const int2* span, int32_t n_items_single,
                   int64_t n_pairs, const int32_t* status, double* out, int64_t* inliers,
-                  cudaStream_t st, int32_t mode) {
+                  cudaStream_t st, int32_t mode, const double* jr, const double* gscale) {
   if (n_pairs <= 0) return VGICP_OK;
   const int warps = 8;
   const int64_t blocks = (n_pairs + warps - 1) / warps;
   reduce_kernel<<<(unsigned)blocks, warps * 32, 0, st>>>(partials, span, n_items_single, n_pairs,
-                                                         status, out, inliers, mode);
+                                                         status, out, inliers, mode, jr, gscale);
   VGICP_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return VGICP_OK;

@@ -14,6 +14,7 @@
 
 #include "vgicp.h"
 #include "vgicp_internal.h"
+#include "vgicp_se3.cuh"
 
 using namespace vgicp;
 
@@ -40,6 +41,8 @@ struct vgicp_plan {
   double* d_partials = nullptr;
   double* d_out = nullptr;
   int64_t* d_inl = nullptr;
+  int2* d_ms = nullptr;          // (map, source) of each pair
+  double* d_jr = nullptr;        // right Jacobians of the last differentiable evaluation
   // host: two pinned staging buffers of the per-pair poses, used alternately;
   // uploaded[b] fires when the copy out of buffer b has completed
   PairDesc* h_pd[2] = {nullptr, nullptr};
@@ -144,6 +147,36 @@ int upload_poses(vgicp_plan* P, int b, cudaStream_t st) {
   VGICP_CUDA_TRY(cudaEventRecord(P->uploaded[b], st));
   P->used[b] = true;
   return VGICP_OK;
+}
+
+// Pose of every factor for a differentiable evaluation, in binary64 on the
+// device: T_p = T0_p Exp(xi_p) (xi = null: T0_p), written as the factor's
+// descriptor, and J_r(xi_p) when jr is given.  A base pose that is not a finite
+// rigid transform, or a non-finite increment, sets the status word (all
+// outputs of the evaluation become NaN) and uses the identity.
+__global__ void compose_kernel(const double* __restrict__ base, const double* __restrict__ xi,
+                               const int2* __restrict__ ms, int64_t n_pairs,
+                               PairDesc* __restrict__ pd, double* __restrict__ jr,
+                               int32_t* __restrict__ status) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  double T0[16], x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, E[16], T[16];
+  for (int i = 0; i < 16; ++i) T0[i] = base[16 * p + i];
+  bool ok = se3::rigid(T0);
+  if (xi)
+    for (int i = 0; i < 6; ++i) {
+      x[i] = xi[6 * p + i];
+      ok = ok && isfinite(x[i]);
+    }
+  if (!ok) {
+    atomicExch(status, 2);
+    for (int i = 0; i < 16; ++i) T0[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < 6; ++i) x[i] = 0.0;
+  }
+  se3::expmap(x, E);
+  se3::pose_mul(T0, E, T);
+  pd[p] = se3::pair_desc(T, ms[p].x, ms[p].y);
+  if (jr) se3::right_jacobian(x, jr + 36 * p);
 }
 
 void drop_graph(vgicp_plan* P) {
@@ -275,7 +308,9 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
   const size_t o_part = take(sizeof(double) * kPartialStride * P->items_cap);
   const size_t o_out = take(sizeof(double) * 43 * n_pairs);
   const size_t o_inl = take(sizeof(int64_t) * n_pairs);
-  cudaError_t e = cudaMalloc(&P->d_block, off);
+  const size_t o_ms = take(sizeof(int2) * n_pairs);
+  const size_t o_jr = take(sizeof(double) * 36 * n_pairs);
+  cudaError_t e = device_malloc(reinterpret_cast<void**>(&P->d_block), off, nullptr, false);
   if (e != cudaSuccess) {
     cudaGetLastError();
     destroy_plan(P);
@@ -290,12 +325,18 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
   P->d_partials = reinterpret_cast<double*>(P->d_block + o_part);
   P->d_out = reinterpret_cast<double*>(P->d_block + o_out);
   P->d_inl = reinterpret_cast<int64_t*>(P->d_block + o_inl);
+  P->d_ms = reinterpret_cast<int2*>(P->d_block + o_ms);
+  P->d_jr = reinterpret_cast<double*>(P->d_block + o_jr);
+  std::vector<int2> ms((size_t)n_pairs);
+  for (int64_t p = 0; p < n_pairs; ++p) ms[(size_t)p] = make_int2(pairs[2 * p], pairs[2 * p + 1]);
   int rc = VGICP_OK;
   if ((e = cudaMallocHost(&P->h_pd[0], sizeof(PairDesc) * n_pairs)) != cudaSuccess ||
       (e = cudaMallocHost(&P->h_pd[1], sizeof(PairDesc) * n_pairs)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&P->uploaded[0], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&P->uploaded[1], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMemcpy(P->d_ms, ms.data(), sizeof(int2) * ms.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(P->d_md, P->md.data(), sizeof(MapDesc) * P->md.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(P->d_sd, P->sd.data(), sizeof(SrcDesc) * P->sd.size(),
@@ -394,6 +435,28 @@ int vgicp_plan_execute(vgicp_plan* P, const double* poses, double* out, int64_t*
     VGICP_CUDA_TRY(cudaMemcpyAsync(inliers, P->d_inl, sizeof(int64_t) * P->n_pairs,
                                    cudaMemcpyDeviceToDevice, st));
   return VGICP_OK;
+}
+
+int vgicp_plan_evaluate(vgicp_plan* P, const double* base_poses, const double* xi, int32_t mode,
+                        const double* grad_scale, double* out, int64_t* inliers,
+                        vgicp_stream_t stream) {
+  if (!P || !base_poses || !out) return set_error(VGICP_ERR_INVALID_ARG, "null plan, poses or out");
+  if (mode < 1 || mode > 3) return set_error(VGICP_ERR_INVALID_ARG, "mode must be 1, 2 or 3");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  VGICP_CUDA_TRY(cudaMemsetAsync(P->d_status, 0, 2 * sizeof(int32_t), st));
+  double* jr = mode >= 2 && xi ? P->d_jr : nullptr;
+  const int64_t n = P->n_pairs;
+  compose_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(base_poses, xi, P->d_ms, n, P->d_pd,
+                                                              jr, P->d_status);
+  VGICP_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  LinLaunch L = launch_of(P);
+  L.mode = mode;
+  int rc = launch_linearize(L, st);
+  if (rc) return rc;
+  // the caller's inlier buffer, or the plan's own
+  return launch_reduce(P->d_partials, P->d_span, 0, n, P->d_status, out,
+                       inliers ? inliers : P->d_inl, st, mode, jr, grad_scale);
 }
 
 int vgicp_plan_info(const vgicp_plan* P, int32_t* variant, int32_t* item_points, int32_t* grid,
