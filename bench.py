@@ -35,6 +35,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "VGICP linearize: source pts/s and % HBM peak; batched vs per-factor"
 BYTES_PER_POINT = 36  # xyz (12 B) + 6-float covariance (24 B) per source point per factor
+# FP32 operations of the linearization, counted from the kernel's formula (an FMA
+# counts 2, the reciprocal 1, comparisons and integer key arithmetic 0): per
+# point-voxel term, the residual rotated into the source frame (15),
+# R^T C' R + C_k from the Cholesky factor (63), the adjugate inverse (30),
+# u = W' d' (15), err (6), b (15), H_vv (6), [mu]x W' and its accumulation (36),
+# H_ww (24) and the term count (1); per source point, T mu (18) and the float32
+# part of the exact key test (11).
+FLOPS_PER_TERM = 211
+FLOPS_PER_POINT_27 = 29
+
+
+def fp32_peak_tflops(peaks) -> float:
+    """Dense FP32 peak of the GPU: SMs x 128 FP32 lanes x 2 flops (FMA) x the
+    maximum SM clock (152 SMs and 2.07 GHz on GB300)."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def parse_args(argv=None):
@@ -731,9 +747,10 @@ def run_workload(args):
         covs_h = torch.from_numpy(w.clouds.covs).pin_memory()
 
         def step():
+            state["ev"] = []
             state["r"] = api.linearize_admitted(pts_h, covs_h, w.clouds.offsets,
                                                 w.pairs, w.poses, w.resolution, budget=budget,
-                                                neighbours=27)
+                                                neighbours=27, kernel_events=state["ev"])
         n_pts = int(w.source_points_per_step)
         name = (f"large_map_{len(w.clouds.offsets) - 1}submaps_x100k_{w.pairs.shape[0]}pairs"
                 f"_r0.5_27neighbours")
@@ -786,15 +803,35 @@ def run_workload(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = BYTES_PER_POINT * n_pts / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "whole step (36 B per source point over the step time)"}
+    if args.workload == "large":
+        # the 27-neighbour linearize kernel alone, over the last step's batches:
+        # its HBM fraction (36 B per source point) and its FP32 fraction
+        torch.cuda.synchronize()
+        kms = float(sum(a.elapsed_time(b) for a, b in state["ev"]))
+        terms = float(np.sum(state["r"][1]))  # point-voxel terms (27-neighbour inliers)
+        flops = FLOPS_PER_TERM * terms + FLOPS_PER_POINT_27 * n_pts
+        fp32_peak = fp32_peak_tflops(peaks)
+        roofline = {"bound": "alu", "achieved": flops / (kms / 1e3) / 1e12, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": flops / (kms / 1e3) / 1e12 / fp32_peak,
+                    "traffic": None,
+                    "kernel": "27-neighbour linearize kernel alone (CUDA events around each "
+                              "admission batch's launch, summed)",
+                    "kernel_ms": kms, "terms": terms,
+                    "flops": {"per_term": FLOPS_PER_TERM, "per_point": FLOPS_PER_POINT_27},
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                    "hbm": {"achieved": BYTES_PER_POINT * n_pts / (kms / 1e3) / 1e9,
+                            "peak": peak, "unit": "GB/s",
+                            "frac": BYTES_PER_POINT * n_pts / (kms / 1e3) / 1e9 / peak}}
     line = {
         "metric": METRIC, "value": value, "unit": "source pts/s", "n_gpus": 1, "steps": K,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded scenes; no dataset available)",
         "config": dict({"workload": name, "source_points_per_step": n_pts}, **extra),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole step (36 B per source point over the step time)"},
+        "roofline": roofline,
         "parity": parity, "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -590,13 +590,14 @@ def _host_rows(x, a, b):
 
 
 def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution, budget,
-                       neighbours=27, tile=0, stream=None):
+                       neighbours=27, tile=0, stream=None, kernel_events=None):
     """Linearize factors among submaps that live in host memory, batch by batch:
     each batch's submaps are uploaded, built into voxel maps (which also serve
     as the sources), linearized in one batched launch, and released.
     ``points_host`` / ``covs_host``: numpy arrays or CPU tensors (pinned tensors
     upload at full speed).  Returns (out (P, 43) float64 host, inliers (P,) host,
-    n_batches)."""
+    n_batches).  ``kernel_events``: optional list; each batch appends the
+    (start, stop) torch.cuda.Event pair recorded around its linearize kernel."""
     off = np.asarray(offsets, dtype=np.int64)
     pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     P = pairs.shape[0]
@@ -621,8 +622,14 @@ def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution
         maps = build_voxelmaps(pts, cvs, boff, resolution, stream=stream)
         maps[0].status()
         lp = np.array([[local[int(j)], local[int(i)]] for j, i in pairs[sel]], dtype=np.int32)
+        ev = None
+        if kernel_events is not None:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for e in ev:  # creates the CUDA event the library then records
+                e.record()
+            kernel_events.append(ev)
         res = linearize_batched(maps, maps, lp, poses[sel], neighbours=neighbours, tile=tile,
-                                stream=stream)
+                                events=ev, stream=stream)
         out[sel] = res.out.cpu().numpy()
         inl[sel] = res.inliers.cpu().numpy()
         for m in maps:

@@ -106,26 +106,37 @@ def test_backward_vs_finite_differences(full_set):
 def test_gradient_descent_refinement_from_perturbed_poses(full_set):
     """Gradient steps preconditioned by H (the backward kernel's gradient and a
     batched linearization at the current poses, re-evaluated every step) from
-    the 0.3 m / 5 deg perturbations."""
+    the 0.3 m / 5 deg perturbations.  The raw cost is a sum over the points that
+    currently have a voxel, so it may grow as a pose improves and more points
+    find one; convergence is judged by the error per inlier and by the pose
+    error against the ground truth."""
     w, maps, srcs, omaps, refs = full_set
     P = w.pairs.shape[0]
+    zero = torch.zeros((P, 6), dtype=torch.float64, device="cuda")
     fs = autograd.FactorSet(maps, srcs, w.pairs, w.poses)
     poses = w.poses.copy()
-    err0 = None
+
+    def per_inlier(poses_now):
+        fs.rebase(poses_now)
+        out, inl = fs.plan.evaluate(fs.base, zero, mode=api.COST)
+        return out[:, 6].cpu().numpy() / np.maximum(inl.cpu().numpy(), 1)
+
+    e0 = per_inlier(poses)
     for _ in range(12):
         fs.rebase(poses)
         lin = api.linearize_batched(maps, srcs, w.pairs, poses)
         H = lin.out[:, :36].reshape(P, 6, 6).cpu().numpy()
-        err, g = _grad(fs, torch.zeros((P, 6), dtype=torch.float64, device="cuda"))
-        if err0 is None:
-            err0 = err.cpu().numpy()
+        _, g = _grad(fs, zero)
         g = g.cpu().numpy()
         for p in range(P):
             poses[p] = poses[p] @ api.se3_exp(-0.5 * np.linalg.solve(H[p], g[p]))
-    fs.rebase(poses)
-    err1 = fs.cost(torch.zeros((P, 6), dtype=torch.float64, device="cuda")).cpu().numpy()
-    assert (err1 < err0).all()
-    rot, tr = zip(*[se3.pose_error(poses[p], w.true_poses[p]) for p in range(P)])
-    rot0, tr0 = zip(*[se3.pose_error(w.poses[p], w.true_poses[p]) for p in range(P)])
-    assert np.median(tr) < 0.3 * np.median(tr0) and np.median(rot) < 0.3 * np.median(rot0), (
-        np.median(tr), np.median(tr0), np.median(rot), np.median(rot0))
+    e1 = per_inlier(poses)
+    rot, tr = map(np.array, zip(*[se3.pose_error(poses[p], w.true_poses[p]) for p in range(P)]))
+    rot0, tr0 = map(np.array, zip(*[se3.pose_error(w.poses[p], w.true_poses[p])
+                                    for p in range(P)]))
+    print(f"median error per inlier {np.median(e0):.3f} -> {np.median(e1):.3f}; median pose "
+          f"error {np.median(tr0):.3f} m / {np.median(rot0):.2f} deg -> {np.median(tr):.4f} m / "
+          f"{np.median(rot):.3f} deg; improved {np.mean(tr < tr0):.3f} / {np.mean(rot < rot0):.3f}")
+    assert np.median(e1) < 0.5 * np.median(e0)
+    assert np.median(tr) < 0.3 * np.median(tr0) and np.median(rot) < 0.3 * np.median(rot0)
+    assert np.mean(tr < tr0) >= 0.9 and np.mean(rot < rot0) >= 0.9
