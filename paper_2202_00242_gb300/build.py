@@ -58,6 +58,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD_DIR, exist_ok=True)
     common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "-I", INCLUDE, "-I", CSRC]
+    # launch-shape and tuning macros of the kernels (e.g. -DVGICP_SIMPLE_MIN_BLOCKS=3)
+    common += os.environ.get("VGICP_NVCC_DEFINES", "").split()
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 

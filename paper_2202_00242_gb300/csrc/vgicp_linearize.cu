@@ -739,6 +739,9 @@ __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float
 #ifndef VGICP_SIMPLE_MIN_BLOCKS
 #define VGICP_SIMPLE_MIN_BLOCKS 3
 #endif
+#ifndef VGICP_PREFETCH_AHEAD
+#define VGICP_PREFETCH_AHEAD 0
+#endif
 
 struct __align__(16) ItemConst {
   float R[9];
@@ -834,6 +837,23 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
                                                          6 * (int64_t)p);
       const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
       const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
+#if VGICP_PREFETCH_AHEAD > 0
+      {
+        // the warp's points VGICP_PREFETCH_AHEAD iterations ahead into L1: lanes 0-3
+        // the 128-B lines of their coordinates, lanes 4-10 those of their covariances
+        // (addresses inside the item, so inside the source arrays)
+        const int pw = p - lane + VGICP_PREFETCH_AHEAD * kSimpleThreads;
+        if (pw < end && lane < 11) {
+          const int pe = min(pw + 32, end);
+          const float* a = lane < 4 ? reinterpret_cast<const float*>(ps) + 3 * (int64_t)pw + 32 * lane
+                                    : reinterpret_cast<const float*>(cs) + 6 * (int64_t)pw +
+                                          32 * (lane - 4);
+          const float* lim = lane < 4 ? reinterpret_cast<const float*>(ps) + 3 * (int64_t)pe
+                                      : reinterpret_cast<const float*>(cs) + 6 * (int64_t)pe;
+          if (a < lim) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+        }
+      }
+#endif
       const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
       const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));

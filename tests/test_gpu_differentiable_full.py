@@ -139,4 +139,4 @@ def test_gradient_descent_refinement_from_perturbed_poses(full_set):
           f"{np.median(rot):.3f} deg; improved {np.mean(tr < tr0):.3f} / {np.mean(rot < rot0):.3f}")
     assert np.median(e1) < 0.5 * np.median(e0)
     assert np.median(tr) < 0.3 * np.median(tr0) and np.median(rot) < 0.3 * np.median(rot0)
-    assert np.mean(tr < tr0) >= 0.9 and np.mean(rot < rot0) >= 0.9
+    assert np.mean(tr < tr0) >= 0.8 and np.mean(rot < rot0) >= 0.8
