@@ -85,11 +85,26 @@ struct PairDesc {
   double t64[3];
 };
 
+// A source cloud: the caller's rows (pts n x 3, covs n x 6), or, when blk is
+// set, a map's voxel-grouped copy in 32-point blocks (see kBlkFloats).
 struct SrcDesc {
-  const float* pts;   // n x 3
-  const float* covs;  // n x 6
+  const float* pts;   // n x 3 (rows)
+  const float* covs;  // n x 6 (rows)
   int64_t n;
+  const float* blk;   // non-null: blocked layout (pts and covs unused)
 };
+
+// Blocked layout of the voxel-grouped copy of a map's cloud: blocks of 32
+// consecutive points, each block 9 arrays of 32 floats (x, y, z, then the
+// covariance entries xx xy xz yy yz zz).  Point p of a map is component k at
+// blk[(p / 32) * kBlkFloats + 32 k + p % 32]; the 32 lanes of a warp reading 32
+// consecutive points read one 128-B line per component.  Each map's copy starts
+// on a block; the tail of its last block is padding.
+constexpr int kBlkPts = 32;
+constexpr int kBlkFloats = 9 * kBlkPts;
+__device__ __forceinline__ const float* blk_point(const float* blk, int64_t p) {
+  return blk + (p >> 5) * kBlkFloats + (p & 31);
+}
 
 // Voxels of a map are put in Morton order in chunks of this many (one CTA sorts
 // one chunk in shared memory).

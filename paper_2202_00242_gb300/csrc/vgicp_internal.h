@@ -70,8 +70,12 @@ struct MapSet {
   uint32_t* d_lslot_of = nullptr; // n_total: lookup-table slot of each voxel (or kNoSlot)
   bool built = false;             // a build has run: the lookup tables hold only its
                                   // voxels and the build table is empty
-  float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
-  float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
+  // the clouds grouped by voxel (voxels in Morton order within chunks of a map,
+  // each voxel's points in index order), in 32-point blocks (kBlkFloats); map m's
+  // copy is blocks [gblk_off[m], gblk_off[m + 1])
+  float* d_gblk = nullptr;
+  std::vector<int64_t> gblk_off;  // n_maps + 1, in blocks
+  int64_t* d_gblk_off = nullptr;  // the same on the device
   uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
   int2* d_chunks = nullptr;       // (map, chunk) pairs for the Morton sort
   int32_t n_chunks = 0;

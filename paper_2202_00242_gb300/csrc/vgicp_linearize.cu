@@ -365,16 +365,49 @@ struct TileDesc {
   int32_t pair, begin, n, item, flags, xyz_off, cov_off, pad;
 };
 
+constexpr int kBlocked = 4;  // TileDesc flag: the tile is whole 32-point blocks
+
+// Stage s holds a tile of the caller's rows (coordinates at buf[s], covariances
+// at buf[s] + kXyzBytes) or kTile / 32 blocks of a blocked source at buf[s].
 struct __align__(16) Smem {
   float4 hits[kNCW][kWarpPts * 3];            // staged voxel records of hits
-  unsigned char xyz[kStages][kXyzBytes];
-  unsigned char cov[kStages][kCovBytes];
+  unsigned char buf[kStages][kXyzBytes + kCovBytes];
   TileDesc desc[kStages];
   uint64_t full[kStages];
   uint64_t empty[kStages];
   float red[kNCW][32];
 };
 static_assert(kXyzBytes % 16 == 0 && kCovBytes % 16 == 0, "bulk-copy alignment");
+static_assert(kTile % kBlkPts == 0 && (kTile / kBlkPts) * kBlkFloats * 4 <= kXyzBytes + kCovBytes,
+              "a tile of blocks fits a stage");
+
+// Point i of a staged tile: x, y, z and the covariance (blocked or rows).
+__device__ __forceinline__ void tile_point(const unsigned char* buf, const TileDesc& d, int i,
+                                           float& x, float& y, float& z) {
+  if (d.flags & kBlocked) {
+    const float* g = blk_point(reinterpret_cast<const float*>(buf), i);
+    x = g[0];
+    y = g[32];
+    z = g[64];
+  } else {
+    const float* X = reinterpret_cast<const float*>(buf + d.xyz_off);
+    x = X[3 * i];
+    y = X[3 * i + 1];
+    z = X[3 * i + 2];
+  }
+}
+__device__ __forceinline__ void tile_cov(const unsigned char* buf, const TileDesc& d, int i,
+                                         float* c) {
+  if (d.flags & kBlocked) {
+    const float* g = blk_point(reinterpret_cast<const float*>(buf), i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c[k] = g[96 + 32 * k];
+  } else {
+    const float2* cv = reinterpret_cast<const float2*>(buf + kXyzBytes + d.cov_off + 24 * i);
+    const float2 c01 = cv[0], c23 = cv[1], c45 = cv[2];
+    c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y; c[4] = c45.x; c[5] = c45.y;
+  }
+}
 
 // Copy the float range [gs, ge) of global memory into shared memory at
 // dst + (gs - floor16(gs)): the 16-B aligned interior with one bulk copy
@@ -468,26 +501,41 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
           break;
         }
         const int n = min(kTile, e - t0);
-        const uintptr_t xs = reinterpret_cast<uintptr_t>(sd.pts + 3 * (int64_t)t0);
-        const uintptr_t cs = reinterpret_cast<uintptr_t>(sd.covs + 6 * (int64_t)t0);
-        // head/tail cp.async and the descriptor, then the two arrivals, then bulk
-        const uintptr_t xe = xs + 12 * (uintptr_t)n, ce = cs + 24 * (uintptr_t)n;
-        const uint32_t tx = stage_range(S.xyz[s], xs, xe, &S.full[s], false, stream_pol) +
-                            stage_range(S.cov[s], cs, ce, &S.full[s], false, stream_pol);
         TileDesc d;
         d.pair = pair;
         d.begin = t0;
         d.n = n;
         d.item = it;
         d.flags = (t0 == b ? kFirst : 0) | (t0 + kTile >= e ? kLast : 0);
-        d.xyz_off = (int)(xs & 15);
-        d.cov_off = (int)(cs & 15);
         d.pad = 0;
-        S.desc[s] = d;
-        cp_async_arrive_noinc(&S.full[s]);
-        mbar_arrive_expect_tx(&S.full[s], tx);
-        stage_range(S.xyz[s], xs, xe, &S.full[s], true, stream_pol);
-        stage_range(S.cov[s], cs, ce, &S.full[s], true, stream_pol);
+        if (sd.blk) {
+          // whole blocks: items and tiles start on a block, and the last block of
+          // a map's copy is allocated in full (its tail is padding)
+          const uint32_t bytes = (uint32_t)((n + kBlkPts - 1) / kBlkPts) * kBlkFloats * 4;
+          d.flags |= kBlocked;
+          d.xyz_off = d.cov_off = 0;
+          S.desc[s] = d;
+          cp_async_arrive_noinc(&S.full[s]);
+          mbar_arrive_expect_tx(&S.full[s], bytes);
+          bulk_g2s(S.buf[s], sd.blk + (int64_t)(t0 / kBlkPts) * kBlkFloats, bytes, &S.full[s],
+                   stream_pol);
+        } else {
+          unsigned char* sx = S.buf[s];
+          unsigned char* sc = S.buf[s] + kXyzBytes;
+          const uintptr_t xs = reinterpret_cast<uintptr_t>(sd.pts + 3 * (int64_t)t0);
+          const uintptr_t cs = reinterpret_cast<uintptr_t>(sd.covs + 6 * (int64_t)t0);
+          // head/tail cp.async and the descriptor, then the two arrivals, then bulk
+          const uintptr_t xe = xs + 12 * (uintptr_t)n, ce = cs + 24 * (uintptr_t)n;
+          const uint32_t tx = stage_range(sx, xs, xe, &S.full[s], false, stream_pol) +
+                              stage_range(sc, cs, ce, &S.full[s], false, stream_pol);
+          d.xyz_off = (int)(xs & 15);
+          d.cov_off = (int)(cs & 15);
+          S.desc[s] = d;
+          cp_async_arrive_noinc(&S.full[s]);
+          mbar_arrive_expect_tx(&S.full[s], tx);
+          stage_range(sx, xs, xe, &S.full[s], true, stream_pol);
+          stage_range(sc, cs, ce, &S.full[s], true, stream_pol);
+        }
         ++u;
       }
     }
@@ -542,8 +590,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       mask = *md.vmask;
       if (L.corr_out) vbase = *md.vbase;
     }
-    const float* X = reinterpret_cast<const float*>(S.xyz[s] + d.xyz_off);
-    const float* C = reinterpret_cast<const float*>(S.cov[s] + d.cov_off);
+    const unsigned char* buf = S.buf[s];
 
     // ---- lookup: key, first probe (two 256-bit loads) of every point, resolve ----
     int idx[kPtsPerLane];
@@ -558,7 +605,8 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       live[k] = idx[k] < d.n;
       kx[k] = ky[k] = kz[k] = kKeyMin - 1;
       if (live[k]) {
-        const float x = X[3 * idx[k]], y = X[3 * idx[k] + 1], z = X[3 * idx[k] + 2];
+        float x, y, z;
+        tile_point(buf, d, idx[k], x, y, z);
         const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
         const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
         const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
@@ -627,10 +675,9 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
     for (int j = lane; j < nh; j += 32) {
       const float4 e0 = H[3 * j], e1 = H[3 * j + 1], e2 = H[3 * j + 2];
       const int i = __float_as_int(e0.w);
-      const float x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
-      const float2* cv = reinterpret_cast<const float2*>(C + 6 * i);
-      const float2 c01 = cv[0], c23 = cv[1], c45 = cv[2];
-      const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
+      float x, y, z, c[6];
+      tile_point(buf, d, i, x, y, z);
+      tile_cov(buf, d, i, c);
       const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
       const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
@@ -739,9 +786,29 @@ __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float
 #ifndef VGICP_SIMPLE_MIN_BLOCKS
 #define VGICP_SIMPLE_MIN_BLOCKS 3
 #endif
-#ifndef VGICP_PREFETCH_AHEAD
-#define VGICP_PREFETCH_AHEAD 0
-#endif
+
+// Source point p: from the caller's rows (cs = covariance rows), or, when cs is
+// 0, from a map's blocked grouped copy at ps (one 128-B line per component for
+// the 32 consecutive points of a warp).
+__device__ __forceinline__ void load_point(uint64_t ps, uint64_t cs, int64_t p, float& x,
+                                           float& y, float& z, float* c) {
+  if (cs) {
+    const float* pt = reinterpret_cast<const float*>(ps) + 3 * p;
+    x = __ldg(pt + 0);
+    y = __ldg(pt + 1);
+    z = __ldg(pt + 2);
+    const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) + 6 * p);
+    const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
+    c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y; c[4] = c45.x; c[5] = c45.y;
+  } else {
+    const float* g = blk_point(reinterpret_cast<const float*>(ps), p);
+    x = __ldg(g);
+    y = __ldg(g + 32);
+    z = __ldg(g + 64);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c[k] = __ldg(g + 96 + 32 * k);
+  }
+}
 
 struct __align__(16) ItemConst {
   float R[9];
@@ -795,8 +862,8 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
       ic.margin_scale = md.margin_scale;
       ic.mask = *md.vmask;
       ic.vslots = md.vslots;
-      ic.pts = sd.pts;
-      ic.covs = sd.covs;
+      ic.pts = sd.blk ? sd.blk : sd.pts;  // blocked sources: covs == null
+      ic.covs = sd.blk ? nullptr : sd.covs;
       ic.pd = pd;
       ic.r = md.r;
       ic.max_probe = md.max_probe;
@@ -831,29 +898,8 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
       const uint32_t mask = __float_as_uint(g3.w);
       const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
 
-      const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
-      const float x = __ldg(pt + 0), y = __ldg(pt + 1), z = __ldg(pt + 2);
-      const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
-                                                         6 * (int64_t)p);
-      const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
-      const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
-#if VGICP_PREFETCH_AHEAD > 0
-      {
-        // the warp's points VGICP_PREFETCH_AHEAD iterations ahead into L1: lanes 0-3
-        // the 128-B lines of their coordinates, lanes 4-10 those of their covariances
-        // (addresses inside the item, so inside the source arrays)
-        const int pw = p - lane + VGICP_PREFETCH_AHEAD * kSimpleThreads;
-        if (pw < end && lane < 11) {
-          const int pe = min(pw + 32, end);
-          const float* a = lane < 4 ? reinterpret_cast<const float*>(ps) + 3 * (int64_t)pw + 32 * lane
-                                    : reinterpret_cast<const float*>(cs) + 6 * (int64_t)pw +
-                                          32 * (lane - 4);
-          const float* lim = lane < 4 ? reinterpret_cast<const float*>(ps) + 3 * (int64_t)pe
-                                      : reinterpret_cast<const float*>(cs) + 6 * (int64_t)pe;
-          if (a < lim) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-        }
-      }
-#endif
+      float x, y, z, c[6];
+      load_point(ps, cs, p, x, y, z, c);
       const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
       const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
@@ -988,8 +1034,8 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
       ic.margin_scale = md.margin_scale;
       ic.mask = *md.vmask;
       ic.vslots = md.vslots;
-      ic.pts = sd.pts;
-      ic.covs = sd.covs;
+      ic.pts = sd.blk ? sd.blk : sd.pts;  // blocked sources: covs == null
+      ic.covs = sd.blk ? nullptr : sd.covs;
       ic.pd = pd;
       ic.r = md.r;
       ic.max_probe = md.max_probe;
@@ -1014,15 +1060,13 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
         uint64_t vs, ps, cs, pds;
         lds_2ptr(&ic.vslots, vs, ps);
         lds_2ptr(&ic.covs, cs, pds);
-        const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
-        x = __ldg(pt + 0);
-        y = __ldg(pt + 1);
-        z = __ldg(pt + 2);
-        const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
-                                                           6 * (int64_t)p);
-        c01 = __ldg(cv + 0);
-        c23 = __ldg(cv + 1);
-        c45 = __ldg(cv + 2);
+        {
+          float cc[6];
+          load_point(ps, cs, p, x, y, z, cc);
+          c01 = make_float2(cc[0], cc[1]);
+          c23 = make_float2(cc[2], cc[3]);
+          c45 = make_float2(cc[4], cc[5]);
+        }
         const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
         const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
         const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
@@ -1104,320 +1148,6 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
 }
 }  // namespace compact
 
-// ---------------------------------------------------------------------------
-// Point-pair kernel (1 neighbour, linearization).  Each thread takes two source
-// points of its work item, p and p + 256, issues both lookups before waiting on
-// either, and evaluates the two points' terms together in packed float32x2
-// arithmetic: one FFMA2 / FMUL2 / FADD2 performs the same operation on both
-// points, each lane rounded exactly as the scalar float32 operation.  The
-// accumulators keep the two points' sums side by side (lane .x for the first
-// point of every pair, .y for the second) and are folded at the end of the item.
-// A point without a voxel (or past the end of the item) contributes zero: its
-// voxel Gaussian is replaced by (q, I) and the reciprocal of its determinant by
-// 0, so W' = 0 and every term vanishes without a branch.
-// ---------------------------------------------------------------------------
-namespace pairk {
-#ifndef VGICP_PAIR_MIN_BLOCKS
-#define VGICP_PAIR_MIN_BLOCKS 2
-#endif
-constexpr int kThreads = 256;
-constexpr int kStride = 2 * kThreads;
-
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-// a b - c d with the product c d rounded first (the scalar form fmaf(a, b, -c * d))
-__device__ __forceinline__ float2 fms2(float2 a, float2 b, float2 c, float2 d) {
-  return fma2(a, b, neg2(mul2(c, d)));
-}
-__device__ __forceinline__ float2 lds_f2(const void* p) {
-  float2 v;
-  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-               : "=f"(v.x), "=f"(v.y)
-               : "r"((uint32_t)__cvta_generic_to_shared(p)));
-  return v;
-}
-
-// The pose as (R_k, R_k) and (t_k, t_k) pairs, for packed operands.
-struct __align__(16) PoseX2 {
-  float2 R[9];
-  float2 t[3];
-};
-
-// Exact voxel key of one transformed point (see source_key); r is read from
-// shared memory only on the rare binary64 path.
-__device__ __forceinline__ void exact_key(const ItemConst& ic, float tmax, float inv_r,
-                                          float margin_scale, const PairDesc* pd, float x,
-                                          float y, float z, float qx, float qy, float qz,
-                                          int& kx, int& ky, int& kz) {
-  const float S = fabsf(x) + fabsf(y) + fabsf(z) + tmax;
-  const float m = fmaf(S, margin_scale, 1.1920928955078125e-7f);
-  const float yx = qx * inv_r, yy = qy * inv_r, yz = qz * inv_r;
-  const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-  const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-  const bool ax = (rx < m) | (rx > 1.0f - m);
-  const bool ay = (ry < m) | (ry > 1.0f - m);
-  const bool az = (rz < m) | (rz > 1.0f - m);
-  kx = clamp_to_int(fx);
-  ky = clamp_to_int(fy);
-  kz = clamp_to_int(fz);
-  if (ax | ay | az) {
-    MapDesc mr;
-    mr.r = ic.r;
-    if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-    if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-    if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-  }
-}
-
-// First probe of a key: home slot and its two 256-bit loads (issued, not waited on).
-__device__ __forceinline__ bool probe_first(const VSlot* vs, uint32_t mask, int kx, int ky,
-                                            int kz, uint64_t pol, uint32_t& h,
-                                            unsigned long long& key, uint32_t (&a)[8],
-                                            uint32_t (&b)[8]) {
-  const bool live = key_in_range(kx) && key_in_range(ky) && key_in_range(kz);
-  key = live ? pack_key(kx, ky, kz) : kEmptyKey;
-  h = hash_key(kx, ky, kz) & mask;
-  if (live) {
-    ld_v8(vs + h, pol, a);
-    ld_v8(reinterpret_cast<const char*>(vs + h) + 32, pol, b);
-  } else {
-    a[0] = a[1] = 0xFFFFFFFFu;
-  }
-  return live;
-}
-
-// The rest of the probe sequence; true if the key was found (a, b then hold its slot).
-__device__ __forceinline__ bool probe_rest(const VSlot* vs, uint32_t mask, int max_probe,
-                                           bool live, uint32_t h, unsigned long long key,
-                                           uint64_t pol, uint32_t (&a)[8], uint32_t (&b)[8]) {
-  if (!live) return false;
-  unsigned long long t = slot_key(a);
-  for (int p = 1; t != key && t != kEmptyKey && (p > 1 || a[7] != 0u) && p < max_probe; ++p) {
-    h = (h + 1) & mask;
-    ld_v8(vs + h, pol, a);
-    ld_v8(reinterpret_cast<const char*>(vs + h) + 32, pol, b);
-    t = slot_key(a);
-  }
-  return t == key;
-}
-
-// Terms of two points at once (the packed form of add_term_t plus the residual).
-__device__ __forceinline__ void add_term2(float2* acc, const PoseX2& PX, float2 x, float2 y,
-                                          float2 z, const float2* c, float2 tx, float2 ty,
-                                          float2 tz, const float2* L, float2 valid) {
-  float2 d0, d1, d2, m00, m01, m02, m11, m12, m22;
-  {
-    const float2 R0 = lds_f2(&PX.R[0]), R1 = lds_f2(&PX.R[1]), R2 = lds_f2(&PX.R[2]);
-    const float2 R3 = lds_f2(&PX.R[3]), R4 = lds_f2(&PX.R[4]), R5 = lds_f2(&PX.R[5]);
-    const float2 R6 = lds_f2(&PX.R[6]), R7 = lds_f2(&PX.R[7]), R8 = lds_f2(&PX.R[8]);
-    // residual in the source frame d' = R^T (mu' - q)
-    d0 = fma2(R0, tx, fma2(R3, ty, mul2(R6, tz)));
-    d1 = fma2(R1, tx, fma2(R4, ty, mul2(R7, tz)));
-    d2 = fma2(R2, tx, fma2(R5, ty, mul2(R8, tz)));
-    // B = R^T L, M' = B B^T + C_k
-    const float2 l00 = L[0], l10 = L[1], l20 = L[2], l11 = L[3], l21 = L[4], l22 = L[5];
-    const float2 b00 = fma2(R0, l00, fma2(R3, l10, mul2(R6, l20)));
-    const float2 b10 = fma2(R1, l00, fma2(R4, l10, mul2(R7, l20)));
-    const float2 b20 = fma2(R2, l00, fma2(R5, l10, mul2(R8, l20)));
-    const float2 b01 = fma2(R3, l11, mul2(R6, l21));
-    const float2 b11 = fma2(R4, l11, mul2(R7, l21));
-    const float2 b21 = fma2(R5, l11, mul2(R8, l21));
-    const float2 b02 = mul2(R6, l22), b12 = mul2(R7, l22), b22 = mul2(R8, l22);
-    m00 = fma2(b00, b00, fma2(b01, b01, fma2(b02, b02, c[0])));
-    m01 = fma2(b00, b10, fma2(b01, b11, fma2(b02, b12, c[1])));
-    m02 = fma2(b00, b20, fma2(b01, b21, fma2(b02, b22, c[2])));
-    m11 = fma2(b10, b10, fma2(b11, b11, fma2(b12, b12, c[3])));
-    m12 = fma2(b10, b20, fma2(b11, b21, fma2(b12, b22, c[4])));
-    m22 = fma2(b20, b20, fma2(b21, b21, fma2(b22, b22, c[5])));
-  }
-  // W' = adj(M') / det(M'), zero for a point without a voxel
-  const float2 i00 = fms2(m11, m22, m12, m12);
-  const float2 i01 = fms2(m02, m12, m01, m22);
-  const float2 i02 = fms2(m01, m12, m02, m11);
-  const float2 i11 = fms2(m00, m22, m02, m02);
-  const float2 i12 = fms2(m01, m02, m00, m12);
-  const float2 i22 = fms2(m00, m11, m01, m01);
-  const float2 det = fma2(m00, i00, fma2(m01, i01, mul2(m02, i02)));
-  const float2 s = mul2(make_float2(rcp_approx(det.x), rcp_approx(det.y)), valid);
-  const float2 w00 = mul2(i00, s), w01 = mul2(i01, s), w02 = mul2(i02, s);
-  const float2 w11 = mul2(i11, s), w12 = mul2(i12, s), w22 = mul2(i22, s);
-  // u = W' d'
-  const float2 u0 = fma2(w00, d0, fma2(w01, d1, mul2(w02, d2)));
-  const float2 u1 = fma2(w01, d0, fma2(w11, d1, mul2(w12, d2)));
-  const float2 u2 = fma2(w02, d0, fma2(w12, d1, mul2(w22, d2)));
-  acc[27] = fma2(d0, u0, fma2(d1, u1, fma2(d2, u2, acc[27])));
-  acc[21] = fma2(u1, z, fma2(neg2(u2), y, acc[21]));
-  acc[22] = fma2(u2, x, fma2(neg2(u0), z, acc[22]));
-  acc[23] = fma2(u0, y, fma2(neg2(u1), x, acc[23]));
-  acc[24] = add2(acc[24], neg2(u0));
-  acc[25] = add2(acc[25], neg2(u1));
-  acc[26] = add2(acc[26], neg2(u2));
-  acc[15] = add2(acc[15], w00); acc[16] = add2(acc[16], w01); acc[17] = add2(acc[17], w02);
-  acc[18] = add2(acc[18], w11); acc[19] = add2(acc[19], w12); acc[20] = add2(acc[20], w22);
-  const float2 p00 = fms2(y, w02, z, w01), p01 = fms2(y, w12, z, w11), p02 = fms2(y, w22, z, w12);
-  const float2 p10 = fms2(z, w00, x, w02), p11 = fms2(z, w01, x, w12), p12 = fms2(z, w02, x, w22);
-  const float2 p20 = fms2(x, w01, y, w00), p21 = fms2(x, w11, y, w01), p22 = fms2(x, w12, y, w02);
-  acc[6] = add2(acc[6], p00); acc[7] = add2(acc[7], p01); acc[8] = add2(acc[8], p02);
-  acc[9] = add2(acc[9], p10); acc[10] = add2(acc[10], p11); acc[11] = add2(acc[11], p12);
-  acc[12] = add2(acc[12], p20); acc[13] = add2(acc[13], p21); acc[14] = add2(acc[14], p22);
-  acc[0] = fma2(p02, y, fma2(neg2(p01), z, acc[0]));
-  acc[1] = fma2(p00, z, fma2(neg2(p02), x, acc[1]));
-  acc[2] = fma2(p01, x, fma2(neg2(p00), y, acc[2]));
-  acc[3] = fma2(p10, z, fma2(neg2(p12), x, acc[3]));
-  acc[4] = fma2(p11, x, fma2(neg2(p10), y, acc[4]));
-  acc[5] = fma2(p21, x, fma2(neg2(p20), y, acc[5]));
-}
-
-__global__ void __launch_bounds__(kThreads, VGICP_PAIR_MIN_BLOCKS)
-    linearize_pair_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ float red[kThreads / 32][kAcc];
-  __shared__ ItemConst ic;
-  __shared__ PoseX2 px;
-  __shared__ int next_item;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t pol = policy_evict_last_l();
-
-  for (int it = blockIdx.x; it < L.n_items;) {
-    int pair, begin, end;
-    tma::item_bounds(L, it, pair, begin, end);
-    if (threadIdx.x == 0) {
-      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        ic.R[k] = pd->R[k];
-        px.R[k] = make_float2(pd->R[k], pd->R[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        ic.t[k] = pd->t[k];
-        px.t[k] = make_float2(pd->t[k], pd->t[k]);
-      }
-      ic.tmax = pd->tmax;
-      ic.inv_r = md.inv_r;
-      ic.margin_scale = md.margin_scale;
-      ic.mask = *md.vmask;
-      ic.vslots = md.vslots;
-      ic.pts = sd.pts;
-      ic.covs = sd.covs;
-      ic.pd = pd;
-      ic.r = md.r;
-      ic.max_probe = md.max_probe;
-    }
-    __syncthreads();
-
-    float2 acc[kTerms];
-#pragma unroll
-    for (int k = 0; k < kTerms; ++k) acc[k] = make_float2(0.0f, 0.0f);
-    int hits = 0;
-
-    // The loop bound is the same for the 32 lanes of a warp (p0 is the warp's
-    // first point), so every lane reaches the warp vote below; a lane whose
-    // point lies past the end reads the item's first point and is masked.
-    for (int p0 = begin + (threadIdx.x & ~31); p0 < end; p0 += kStride) {
-      const int pr = p0 + lane;
-      const bool has_a = pr < end;
-      const int p = has_a ? pr : begin;
-      const int pb = pr + kThreads;
-      const bool has_b = pb < end;
-      const int pq = has_b ? pb : p;  // past the end: re-read p, masked below
-      const float4 g3 = lds_f4(&ic.tmax);
-      uint64_t vs_, ps_, cs_, pds_;
-      lds_2ptr(&ic.vslots, vs_, ps_);
-      lds_2ptr(&ic.covs, cs_, pds_);
-      const VSlot* vs = reinterpret_cast<const VSlot*>(vs_);
-      const float* pts = reinterpret_cast<const float*>(ps_);
-      const float2* cvs = reinterpret_cast<const float2*>(cs_);
-      const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds_);
-      const uint32_t mask = __float_as_uint(g3.w);
-
-      const float2 X = make_float2(__ldg(pts + 3 * (int64_t)p), __ldg(pts + 3 * (int64_t)pq));
-      const float2 Y =
-          make_float2(__ldg(pts + 3 * (int64_t)p + 1), __ldg(pts + 3 * (int64_t)pq + 1));
-      const float2 Z =
-          make_float2(__ldg(pts + 3 * (int64_t)p + 2), __ldg(pts + 3 * (int64_t)pq + 2));
-      float2 C[6];
-      {
-        const float2 a01 = __ldg(cvs + 3 * (int64_t)p), a23 = __ldg(cvs + 3 * (int64_t)p + 1),
-                     a45 = __ldg(cvs + 3 * (int64_t)p + 2);
-        const float2 b01 = __ldg(cvs + 3 * (int64_t)pq), b23 = __ldg(cvs + 3 * (int64_t)pq + 1),
-                     b45 = __ldg(cvs + 3 * (int64_t)pq + 2);
-        C[0] = make_float2(a01.x, b01.x);
-        C[1] = make_float2(a01.y, b01.y);
-        C[2] = make_float2(a23.x, b23.x);
-        C[3] = make_float2(a23.y, b23.y);
-        C[4] = make_float2(a45.x, b45.x);
-        C[5] = make_float2(a45.y, b45.y);
-      }
-      float2 Qx, Qy, Qz;
-      {
-        const float2 R0 = lds_f2(&px.R[0]), R1 = lds_f2(&px.R[1]), R2 = lds_f2(&px.R[2]);
-        Qx = fma2(R0, X, fma2(R1, Y, fma2(R2, Z, lds_f2(&px.t[0]))));
-        const float2 R3 = lds_f2(&px.R[3]), R4 = lds_f2(&px.R[4]), R5 = lds_f2(&px.R[5]);
-        Qy = fma2(R3, X, fma2(R4, Y, fma2(R5, Z, lds_f2(&px.t[1]))));
-        const float2 R6 = lds_f2(&px.R[6]), R7 = lds_f2(&px.R[7]), R8 = lds_f2(&px.R[8]);
-        Qz = fma2(R6, X, fma2(R7, Y, fma2(R8, Z, lds_f2(&px.t[2]))));
-      }
-      int kxa, kya, kza, kxb, kyb, kzb;
-      exact_key(ic, g3.x, g3.y, g3.z, pd, X.x, Y.x, Z.x, Qx.x, Qy.x, Qz.x, kxa, kya, kza);
-      exact_key(ic, g3.x, g3.y, g3.z, pd, X.y, Y.y, Z.y, Qx.y, Qy.y, Qz.y, kxb, kyb, kzb);
-      uint32_t ha, hb;
-      unsigned long long keya, keyb;
-      uint32_t sa[8], sb[8], ta[8], tb[8];
-      const bool la = probe_first(vs, mask, kxa, kya, kza, pol, ha, keya, sa, sb) && has_a;
-      const bool lb = probe_first(vs, mask, kxb, kyb, kzb, pol, hb, keyb, ta, tb) && has_b;
-      const int max_probe = ic.max_probe;
-      const bool hit_a = probe_rest(vs, mask, max_probe, la, ha, keya, pol, sa, sb);
-      const bool hit_b = probe_rest(vs, mask, max_probe, lb, hb, keyb, pol, ta, tb);
-      if (!__any_sync(0xFFFFFFFFu, hit_a || hit_b)) continue;
-      hits += (int)hit_a + (int)hit_b;
-      // residual mu' - q and the voxel's Cholesky factor; (q, I) for a miss
-      const float2 tx = add2(make_float2(hit_a ? __uint_as_float(sa[4]) : Qx.x,
-                                         hit_b ? __uint_as_float(ta[4]) : Qx.y), neg2(Qx));
-      const float2 ty = add2(make_float2(hit_a ? __uint_as_float(sa[5]) : Qy.x,
-                                         hit_b ? __uint_as_float(ta[5]) : Qy.y), neg2(Qy));
-      const float2 tz = add2(make_float2(hit_a ? __uint_as_float(sa[6]) : Qz.x,
-                                         hit_b ? __uint_as_float(ta[6]) : Qz.y), neg2(Qz));
-      float2 Lc[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const float id = (k == 0 || k == 3 || k == 5) ? 1.0f : 0.0f;
-        Lc[k] = make_float2(hit_a ? __uint_as_float(sb[k]) : id, hit_b ? __uint_as_float(tb[k]) : id);
-      }
-      const float2 valid = make_float2(hit_a ? 1.0f : 0.0f, hit_b ? 1.0f : 0.0f);
-      add_term2(acc, px, X, Y, Z, C, tx, ty, tz, Lc, valid);
-    }
-
-    float a[kAcc];
-#pragma unroll
-    for (int k = 0; k < kTerms; ++k) a[k] = acc[k].x + acc[k].y;
-    a[kTerms] = (float)hits;
-#pragma unroll
-    for (int k = 0; k < kAcc; ++k) {
-      float v = a[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-      a[k] = v;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < kAcc; ++k) red[warp][k] = a[k];
-    }
-    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
-    __syncthreads();
-    if (threadIdx.x < kAcc) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][threadIdx.x];
-      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
-    }
-    it = next_item;  // read between the two barriers; rewritten only after the second
-    __syncthreads();
-  }
-}
-}  // namespace pairk
 
 // One warp per pair: lane k sums term k over the pair's items in order.  For the
 // gradient modes, an optional right Jacobian per pair (jr, 36 doubles, row-major)
@@ -1519,7 +1249,6 @@ int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
   if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
   if (variant == 3) return device_sm_count() * VGICP_COMPACT_MIN_BLOCKS;
-  if (variant == 4) return device_sm_count() * VGICP_PAIR_MIN_BLOCKS;
   return device_sm_count() * VGICP_MIN_BLOCKS;
 }
 
@@ -1545,10 +1274,6 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
-  } else if (variant == 4 && !L.corr_out && !L.qkey_out) {
-    pairk::linearize_pair_kernel<<<grid, pairk::kThreads, 0, st>>>(L);
-  } else if (variant == 4) {
-    launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
     compact::linearize_compact_kernel<<<grid, compact::kThreads, 0, st>>>(L);
   } else if (variant == 3) {
