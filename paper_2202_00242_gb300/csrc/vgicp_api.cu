@@ -32,6 +32,12 @@ uint32_t next_pow2(uint64_t x) {
 
 bool finite_pose(const double* T) { return se3::rigid(T); }
 
+int sources_layout(const SrcDesc* sd, size_t n) {
+  size_t blocked = 0;
+  for (size_t i = 0; i < n; ++i) blocked += sd[i].blk ? 1 : 0;
+  return blocked == 0 ? kRows : blocked == n ? kBlocked : kMixed;
+}
+
 PairDesc make_pair_desc(const double* T, int32_t map, int32_t src) {
   return se3::pair_desc(T, map, src);
 }
@@ -431,8 +437,8 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   int item = opts && opts->tile > 0 ? opts->tile : 0;
@@ -526,8 +532,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -628,6 +634,7 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     L.pairs = reinterpret_cast<const PairDesc*>(dev + o_pd);
     L.maps = reinterpret_cast<const MapDesc*>(dev + o_md);
     L.srcs = reinterpret_cast<const SrcDesc*>(dev + o_sd);
+    L.src_layout = sources_layout(sd.data(), sd.size());
     L.partials = reinterpret_cast<double*>(dev + o_part);
     L.status = reinterpret_cast<int32_t*>(dev + o_status);
     L.neighbours = neighbours;
@@ -706,8 +713,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =

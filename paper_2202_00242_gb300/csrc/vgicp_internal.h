@@ -110,6 +110,10 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max,
 size_t scan_tmp_elems(int64_t n_max);
 
 // ---- kernels (vgicp_linearize.cu) ----------------------------------------
+constexpr int kRows = 0, kBlocked = 1, kMixed = 2;  // source layouts of a launch
+// The layout of a set of sources (kRows for none).
+int sources_layout(const SrcDesc* sd, size_t n);
+
 struct LinLaunch {
   const WorkItem* items;     // null: uniform items of pair 0 (single factor)
   int32_t n_items;
@@ -132,6 +136,8 @@ struct LinLaunch {
   int32_t grid;              // 0 = automatic
   cudaEvent_t ev_start;      // optional, recorded around the kernel
   cudaEvent_t ev_stop;
+  int32_t src_layout;        // kRows: every source is the caller's rows; kBlocked: every
+                             // source is a map's blocked copy; kMixed: both
   int64_t wait_limit_ns;     // staged kernel: bound of its mbarrier waits (0 = 2 s)
   int32_t test_withhold_tile;  // staged kernel, tests only: 1 + the tile index each
                                // producer withholds (0 = none)

@@ -787,17 +787,20 @@ __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float
 #define VGICP_SIMPLE_MIN_BLOCKS 3
 #endif
 
-// Source point p: from the caller's rows (cs = covariance rows), or, when cs is
-// 0, from a map's blocked grouped copy at ps (one 128-B line per component for
-// the 32 consecutive points of a warp).
-__device__ __forceinline__ void load_point(uint64_t ps, uint64_t cs, int64_t p, float& x,
-                                           float& y, float& z, float* c) {
-  if (cs) {
-    const float* pt = reinterpret_cast<const float*>(ps) + 3 * p;
+// Source point p: from the caller's rows (ps, cs: coordinate and covariance
+// rows), or (BLK) from a map's blocked grouped copy at ps (one 128-B line per
+// component for the 32 consecutive points of a warp).  The layout is a template
+// parameter so that a point loop holds the loads of one layout only.
+template <bool BLK>
+__device__ __forceinline__ void load_point(uint64_t ps, uint64_t cs, int p, float& x, float& y,
+                                           float& z, float* c) {
+  if (!BLK) {
+    const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
     x = __ldg(pt + 0);
     y = __ldg(pt + 1);
     z = __ldg(pt + 2);
-    const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) + 6 * p);
+    const float2* cv =
+        reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) + 6 * (int64_t)p);
     const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
     c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y; c[4] = c45.x; c[5] = c45.y;
   } else {
@@ -836,7 +839,90 @@ __device__ __forceinline__ void lds_2ptr(const void* p, uint64_t& a, uint64_t& b
                : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
 
-template <int NEIGH, int MODE, bool DBG>
+// The points [begin, end) of one work item, one per thread, accumulated into
+// acc.  Instantiated per source layout (BLK), so that the loop holds the loads of
+// one layout only (a branch on the layout inside the loop is turned into
+// predicated loads of both).
+template <int NEIGH, int MODE, bool DBG, bool BLK>
+__device__ __forceinline__ void simple_points(const LinLaunch& L, const ItemConst& ic, int begin,
+                                              int end, uint32_t vbase, uint64_t pol,
+                                              float (&acc)[kAcc]) {
+  for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
+    const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+    const float4 g3 = lds_f4(&ic.tmax);
+    uint64_t vs, ps, cs, pds;
+    lds_2ptr(&ic.vslots, vs, ps);
+    lds_2ptr(&ic.covs, cs, pds);
+    Pose32 P;
+    P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
+    P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
+    P.R[8] = g2.x;
+    P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
+    P.tmax = g3.x;
+    MapDesc md;
+    md.vslots = reinterpret_cast<const VSlot*>(vs);
+    md.inv_r = g3.y;
+    md.margin_scale = g3.z;
+    const uint32_t mask = __float_as_uint(g3.w);
+    const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+
+    float x, y, z, c[6];
+    load_point<BLK>(ps, cs, p, x, y, z, c);
+    const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+    const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+    const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+    int kx, ky, kz;
+    {
+      // the binary64 fallback reads r from shared memory only when taken
+      const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
+      const float m = fmaf(S, md.margin_scale, 1.1920928955078125e-7f);
+      const float yx = qx * md.inv_r, yy = qy * md.inv_r, yz = qz * md.inv_r;
+      const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+      const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+      const bool ax = (rx < m) | (rx > 1.0f - m);
+      const bool ay = (ry < m) | (ry > 1.0f - m);
+      const bool az = (rz < m) | (rz > 1.0f - m);
+      kx = clamp_to_int(fx);
+      ky = clamp_to_int(fy);
+      kz = clamp_to_int(fz);
+      if (ax | ay | az) {
+        MapDesc mr;
+        mr.r = ic.r;
+        if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+        if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+        if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+      }
+    }
+    if (DBG && L.qkey_out) {
+      L.qkey_out[3 * (int64_t)p + 0] = kx;
+      L.qkey_out[3 * (int64_t)p + 1] = ky;
+      L.qkey_out[3 * (int64_t)p + 2] = kz;
+    }
+    md.max_probe = ic.max_probe;
+    if (NEIGH == 1) {
+      float4 a0, a1, a2;
+      const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+      if (DBG && L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+      if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+      continue;
+    }
+    if (DBG && L.corr_out) {
+      float4 a0, a1, a2;
+      const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+      L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
+    }
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          float4 a0, a1, a2;
+          const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
+          if (vid < 0) continue;
+          term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+        }
+  }
+}
+
+template <int NEIGH, int MODE, bool DBG, int LAYOUT>
 __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
     linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kSimpleThreads / 32][kAcc];
@@ -879,79 +965,10 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
 
-    for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
-      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-      const float4 g3 = lds_f4(&ic.tmax);
-      uint64_t vs, ps, cs, pds;
-      lds_2ptr(&ic.vslots, vs, ps);
-      lds_2ptr(&ic.covs, cs, pds);
-      Pose32 P;
-      P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
-      P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
-      P.R[8] = g2.x;
-      P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
-      P.tmax = g3.x;
-      MapDesc md;
-      md.vslots = reinterpret_cast<const VSlot*>(vs);
-      md.inv_r = g3.y;
-      md.margin_scale = g3.z;
-      const uint32_t mask = __float_as_uint(g3.w);
-      const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
-
-      float x, y, z, c[6];
-      load_point(ps, cs, p, x, y, z, c);
-      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-      int kx, ky, kz;
-      {
-        // the binary64 fallback reads r from shared memory only when taken
-        const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
-        const float m = fmaf(S, md.margin_scale, 1.1920928955078125e-7f);
-        const float yx = qx * md.inv_r, yy = qy * md.inv_r, yz = qz * md.inv_r;
-        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-        const bool ax = (rx < m) | (rx > 1.0f - m);
-        const bool ay = (ry < m) | (ry > 1.0f - m);
-        const bool az = (rz < m) | (rz > 1.0f - m);
-        kx = clamp_to_int(fx);
-        ky = clamp_to_int(fy);
-        kz = clamp_to_int(fz);
-        if (ax | ay | az) {
-          MapDesc mr;
-          mr.r = ic.r;
-          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-        }
-      }
-      if (DBG && L.qkey_out) {
-        L.qkey_out[3 * (int64_t)p + 0] = kx;
-        L.qkey_out[3 * (int64_t)p + 1] = ky;
-        L.qkey_out[3 * (int64_t)p + 2] = kz;
-      }
-      md.max_probe = ic.max_probe;
-      if (NEIGH == 1) {
-        float4 a0, a1, a2;
-        const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-        if (DBG && L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-        if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
-        continue;
-      }
-      if (DBG && L.corr_out) {
-        float4 a0, a1, a2;
-        const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-        L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
-      }
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            float4 a0, a1, a2;
-            const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
-            if (vid < 0) continue;
-            term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
-          }
-    }
+    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
+      simple_points<NEIGH, MODE, DBG, false>(L, ic, begin, end, vbase, pol, acc);
+    else
+      simple_points<NEIGH, MODE, DBG, true>(L, ic, begin, end, vbase, pol, acc);
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -978,10 +995,14 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
 
 template <int NEIGH, int MODE>
 void launch_simple(const LinLaunch& L, int grid, cudaStream_t st) {
-  if (L.corr_out || L.qkey_out)
-    linearize_simple_kernel<NEIGH, MODE, true><<<grid, kSimpleThreads, 0, st>>>(L);
+  if (L.corr_out || L.qkey_out)  // single factor, the caller's rows
+    linearize_simple_kernel<NEIGH, MODE, true, kRows><<<grid, kSimpleThreads, 0, st>>>(L);
+  else if (L.src_layout == kRows)
+    linearize_simple_kernel<NEIGH, MODE, false, kRows><<<grid, kSimpleThreads, 0, st>>>(L);
+  else if (L.src_layout == kBlocked)
+    linearize_simple_kernel<NEIGH, MODE, false, kBlocked><<<grid, kSimpleThreads, 0, st>>>(L);
   else
-    linearize_simple_kernel<NEIGH, MODE, false><<<grid, kSimpleThreads, 0, st>>>(L);
+    linearize_simple_kernel<NEIGH, MODE, false, kMixed><<<grid, kSimpleThreads, 0, st>>>(L);
 }
 
 // ---------------------------------------------------------------------------
@@ -1006,6 +1027,92 @@ __device__ __forceinline__ void eval_entry(float* acc, const float* R, const flo
   add_term_t(acc, R, e0.x, e0.y, e0.z, c, e2.y, e2.z, e2.w, e3, e4);
 }
 
+// The points of one work item (see the kernel); instantiated per source layout.
+template <bool BLK>
+__device__ __forceinline__ void compact_points(const ItemConst& ic, int begin, int end,
+                                               uint64_t pol, float (&acc)[kAcc], float4* Q,
+                                               int lane, int warp, uint32_t lt_mask) {
+  int qn = 0;  // queued entries (warp-uniform)
+  const int n = end - begin;
+
+  for (int base = warp * 32; base < n; base += kThreads) {
+    const int p = begin + base + lane;
+    bool hit = false;
+    float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+    float2 c01, c23, c45;
+    float4 a1, a2;
+    if (p < end) {
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float4 g3 = lds_f4(&ic.tmax);
+      uint64_t vs, ps, cs, pds;
+      lds_2ptr(&ic.vslots, vs, ps);
+      lds_2ptr(&ic.covs, cs, pds);
+      {
+        float cc[6];
+        load_point<BLK>(ps, cs, p, x, y, z, cc);
+        c01 = make_float2(cc[0], cc[1]);
+        c23 = make_float2(cc[2], cc[3]);
+        c45 = make_float2(cc[4], cc[5]);
+      }
+      const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
+      const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
+      const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
+      const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
+      const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
+      const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
+      const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+      const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+      const bool ax = (rx < m) | (rx > 1.0f - m);
+      const bool ay = (ry < m) | (ry > 1.0f - m);
+      const bool az = (rz < m) | (rz > 1.0f - m);
+      int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
+      if (ax | ay | az) {
+        const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+        MapDesc mr;
+        mr.r = ic.r;
+        if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+        if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+        if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+      }
+      MapDesc md;
+      md.vslots = reinterpret_cast<const VSlot*>(vs);
+      md.max_probe = ic.max_probe;
+      float4 a0;
+      const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
+      hit = vid >= 0;
+      tx = a0.x - qx;
+      ty = a0.y - qy;
+      tz = a0.z - qz;
+    }
+    const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+    if (hit) {
+      float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
+      E[0] = make_float4(x, y, z, c01.x);
+      E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
+      E[2] = make_float4(c45.y, tx, ty, tz);
+      E[3] = a1;
+      E[4] = a2;
+    }
+    if (lane == 0) acc[28] += (float)__popc(hm);
+    qn += __popc(hm);
+    __syncwarp();
+    if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+      eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  if (lane < qn) {  // drain the partially filled queue
+    const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+    const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+    eval_entry(acc, R, Q + 5 * lane);
+  }
+  __syncwarp();
+}
+
+template <int LAYOUT>
 __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     linearize_compact_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
@@ -1045,84 +1152,10 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     float acc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
-    int qn = 0;  // queued entries (warp-uniform)
-    const int n = end - begin;
-
-    for (int base = warp * 32; base < n; base += kThreads) {
-      const int p = begin + base + lane;
-      bool hit = false;
-      float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-      float2 c01, c23, c45;
-      float4 a1, a2;
-      if (p < end) {
-        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-        const float4 g3 = lds_f4(&ic.tmax);
-        uint64_t vs, ps, cs, pds;
-        lds_2ptr(&ic.vslots, vs, ps);
-        lds_2ptr(&ic.covs, cs, pds);
-        {
-          float cc[6];
-          load_point(ps, cs, p, x, y, z, cc);
-          c01 = make_float2(cc[0], cc[1]);
-          c23 = make_float2(cc[2], cc[3]);
-          c45 = make_float2(cc[4], cc[5]);
-        }
-        const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
-        const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
-        const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
-        const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
-        const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
-        const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
-        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-        const bool ax = (rx < m) | (rx > 1.0f - m);
-        const bool ay = (ry < m) | (ry > 1.0f - m);
-        const bool az = (rz < m) | (rz > 1.0f - m);
-        int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
-        if (ax | ay | az) {
-          const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
-          MapDesc mr;
-          mr.r = ic.r;
-          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-        }
-        MapDesc md;
-        md.vslots = reinterpret_cast<const VSlot*>(vs);
-        md.max_probe = ic.max_probe;
-        float4 a0;
-        const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
-        hit = vid >= 0;
-        tx = a0.x - qx;
-        ty = a0.y - qy;
-        tz = a0.z - qz;
-      }
-      const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
-      if (hit) {
-        float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
-        E[0] = make_float4(x, y, z, c01.x);
-        E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
-        E[2] = make_float4(c45.y, tx, ty, tz);
-        E[3] = a1;
-        E[4] = a2;
-      }
-      if (lane == 0) acc[28] += (float)__popc(hm);
-      qn += __popc(hm);
-      __syncwarp();
-      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
-        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-        const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
-        eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
-        qn -= 32;
-        __syncwarp();
-      }
-    }
-    if (lane < qn) {  // drain the partially filled queue
-      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-      const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
-      eval_entry(acc, R, Q + 5 * lane);
-    }
-    __syncwarp();
+    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
+      compact_points<false>(ic, begin, end, pol, acc, Q, lane, warp, lt_mask);
+    else
+      compact_points<true>(ic, begin, end, pol, acc, Q, lane, warp, lt_mask);
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -1176,13 +1209,14 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Exact key of source point p of the item's source (x, y, z loaded here).
+template <bool BLK>
 __device__ __forceinline__ void point_key(const ItemConst& icr, uint64_t ps, uint64_t cs,
-                                          int64_t p, const Pose32& P, float inv_r,
+                                          int p, const Pose32& P, float inv_r,
                                           float margin_scale, const PairDesc* pd, int& kx,
                                           int& ky, int& kz) {
   float x, y, z;
-  if (cs) {
-    const float* pt = reinterpret_cast<const float*>(ps) + 3 * p;
+  if (!BLK) {
+    const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
     x = __ldg(pt + 0);
     y = __ldg(pt + 1);
     z = __ldg(pt + 2);
@@ -1233,6 +1267,107 @@ __device__ __forceinline__ void item_consts(const ItemConst& ic, Pose32& P, uint
   mask = __float_as_uint(g3.w);
 }
 
+// The points of one work item (see the kernel); instantiated per source layout.
+template <bool BLK>
+__device__ __forceinline__ void piped_points(const ItemConst& ic, int begin, int end,
+                                             uint64_t pol, float (&acc)[kAcc],
+                                             uint4 (*sbuf)[4][kThreads], int tid) {
+  // the lookup state of the thread's current point (its home slot is in flight
+  // to, or has reached, sbuf[b])
+  unsigned long long key_c = kEmptyKey;
+  uint32_t h_c = 0;
+  int b = 0;
+  int p = begin + tid;
+  {
+    Pose32 P;
+    uint64_t vs, ps, cs, pds;
+    float inv_r, margin;
+    uint32_t mask;
+    item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
+    if (p < end) {
+      int kx, ky, kz;
+      point_key<BLK>(ic, ps, cs, p, P, inv_r, margin, reinterpret_cast<const PairDesc*>(pds), kx,
+                ky, kz);
+      if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
+        key_c = pack_key(kx, ky, kz);
+        h_c = hash_key(kx, ky, kz) & mask;
+        const char* src = reinterpret_cast<const char*>(reinterpret_cast<const VSlot*>(vs) + h_c);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async16(&sbuf[0][c][tid], src + 16 * c, pol);
+      }
+    }
+    cp_async_commit();
+  }
+
+  for (; p < end; p += kThreads, b ^= 1) {
+    Pose32 P;
+    uint64_t vs, ps, cs, pds;
+    float inv_r, margin;
+    uint32_t mask;
+    item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
+    const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+    const VSlot* vslots = reinterpret_cast<const VSlot*>(vs);
+    // start the next point's lookup
+    unsigned long long key_n = kEmptyKey;
+    uint32_t h_n = 0;
+    const int pn = p + kThreads;
+    if (pn < end) {
+      int kx, ky, kz;
+      point_key<BLK>(ic, ps, cs, pn, P, inv_r, margin, pd, kx, ky, kz);
+      if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
+        key_n = pack_key(kx, ky, kz);
+        h_n = hash_key(kx, ky, kz) & mask;
+        const char* src = reinterpret_cast<const char*>(vslots + h_n);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async16(&sbuf[b ^ 1][c][tid], src + 16 * c, pol);
+      }
+    }
+    cp_async_commit();
+    // the current point
+    float x, y, z, c[6];
+    load_point<BLK>(ps, cs, p, x, y, z, c);
+    const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+    const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+    const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+    cp_async_wait<1>();  // this thread's copy of the current point's home slot
+    if (key_c != kEmptyKey) {
+      uint32_t a[8], bb[8];
+      {
+        const uint4 s0 = sbuf[b][0][tid], s1 = sbuf[b][1][tid];
+        const uint4 s2 = sbuf[b][2][tid], s3 = sbuf[b][3][tid];
+        a[0] = s0.x; a[1] = s0.y; a[2] = s0.z; a[3] = s0.w;
+        a[4] = s1.x; a[5] = s1.y; a[6] = s1.z; a[7] = s1.w;
+        bb[0] = s2.x; bb[1] = s2.y; bb[2] = s2.z; bb[3] = s2.w;
+        bb[4] = s3.x; bb[5] = s3.y; bb[6] = s3.z; bb[7] = s3.w;
+      }
+      unsigned long long t = slot_key(a);
+      if (t != key_c && t != kEmptyKey && a[7] != 0u) {  // probe on (rare)
+        uint32_t hh = h_c;
+        const int max_probe = ic.max_probe;
+        for (int q = 1; q < max_probe; ++q) {
+          hh = (hh + 1) & mask;
+          ld_v8(vslots + hh, pol, a);
+          ld_v8(reinterpret_cast<const char*>(vslots + hh) + 32, pol, bb);
+          t = slot_key(a);
+          if (t == key_c || t == kEmptyKey) break;
+        }
+      }
+      if (t == key_c) {
+        const float4 r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]),
+                                      __uint_as_float(a[6]), 0.f);
+        const float4 r1 = make_float4(__uint_as_float(bb[0]), __uint_as_float(bb[1]),
+                                      __uint_as_float(bb[2]), __uint_as_float(bb[3]));
+        const float4 r2 = make_float4(__uint_as_float(bb[4]), __uint_as_float(bb[5]), 0.f, 0.f);
+        add_term(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
+      }
+    }
+    key_c = key_n;
+    h_c = h_n;
+  }
+  cp_async_wait<0>();  // nothing in flight into sbuf when the next item starts
+}
+
+template <int LAYOUT>
 __global__ void __launch_bounds__(kThreads, VGICP_SIMPLE_MIN_BLOCKS)
     linearize_piped_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kThreads / 32][kAcc];
@@ -1271,99 +1406,10 @@ __global__ void __launch_bounds__(kThreads, VGICP_SIMPLE_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
 
-    // the lookup state of the thread's current point (its home slot is in flight
-    // to, or has reached, sbuf[b])
-    unsigned long long key_c = kEmptyKey;
-    uint32_t h_c = 0;
-    int b = 0;
-    int p = begin + tid;
-    {
-      Pose32 P;
-      uint64_t vs, ps, cs, pds;
-      float inv_r, margin;
-      uint32_t mask;
-      item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
-      if (p < end) {
-        int kx, ky, kz;
-        point_key(ic, ps, cs, p, P, inv_r, margin, reinterpret_cast<const PairDesc*>(pds), kx,
-                  ky, kz);
-        if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
-          key_c = pack_key(kx, ky, kz);
-          h_c = hash_key(kx, ky, kz) & mask;
-          const char* src = reinterpret_cast<const char*>(reinterpret_cast<const VSlot*>(vs) + h_c);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) cp_async16(&sbuf[0][c][tid], src + 16 * c, pol);
-        }
-      }
-      cp_async_commit();
-    }
-
-    for (; p < end; p += kThreads, b ^= 1) {
-      Pose32 P;
-      uint64_t vs, ps, cs, pds;
-      float inv_r, margin;
-      uint32_t mask;
-      item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
-      const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
-      const VSlot* vslots = reinterpret_cast<const VSlot*>(vs);
-      // start the next point's lookup
-      unsigned long long key_n = kEmptyKey;
-      uint32_t h_n = 0;
-      const int pn = p + kThreads;
-      if (pn < end) {
-        int kx, ky, kz;
-        point_key(ic, ps, cs, pn, P, inv_r, margin, pd, kx, ky, kz);
-        if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
-          key_n = pack_key(kx, ky, kz);
-          h_n = hash_key(kx, ky, kz) & mask;
-          const char* src = reinterpret_cast<const char*>(vslots + h_n);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) cp_async16(&sbuf[b ^ 1][c][tid], src + 16 * c, pol);
-        }
-      }
-      cp_async_commit();
-      // the current point
-      float x, y, z, c[6];
-      load_point(ps, cs, p, x, y, z, c);
-      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-      cp_async_wait<1>();  // this thread's copy of the current point's home slot
-      if (key_c != kEmptyKey) {
-        uint32_t a[8], bb[8];
-        {
-          const uint4 s0 = sbuf[b][0][tid], s1 = sbuf[b][1][tid];
-          const uint4 s2 = sbuf[b][2][tid], s3 = sbuf[b][3][tid];
-          a[0] = s0.x; a[1] = s0.y; a[2] = s0.z; a[3] = s0.w;
-          a[4] = s1.x; a[5] = s1.y; a[6] = s1.z; a[7] = s1.w;
-          bb[0] = s2.x; bb[1] = s2.y; bb[2] = s2.z; bb[3] = s2.w;
-          bb[4] = s3.x; bb[5] = s3.y; bb[6] = s3.z; bb[7] = s3.w;
-        }
-        unsigned long long t = slot_key(a);
-        if (t != key_c && t != kEmptyKey && a[7] != 0u) {  // probe on (rare)
-          uint32_t hh = h_c;
-          const int max_probe = ic.max_probe;
-          for (int q = 1; q < max_probe; ++q) {
-            hh = (hh + 1) & mask;
-            ld_v8(vslots + hh, pol, a);
-            ld_v8(reinterpret_cast<const char*>(vslots + hh) + 32, pol, bb);
-            t = slot_key(a);
-            if (t == key_c || t == kEmptyKey) break;
-          }
-        }
-        if (t == key_c) {
-          const float4 r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]),
-                                        __uint_as_float(a[6]), 0.f);
-          const float4 r1 = make_float4(__uint_as_float(bb[0]), __uint_as_float(bb[1]),
-                                        __uint_as_float(bb[2]), __uint_as_float(bb[3]));
-          const float4 r2 = make_float4(__uint_as_float(bb[4]), __uint_as_float(bb[5]), 0.f, 0.f);
-          add_term(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
-        }
-      }
-      key_c = key_n;
-      h_c = h_n;
-    }
-    cp_async_wait<0>();  // nothing in flight into sbuf when the next item starts
+    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
+      piped_points<false>(ic, begin, end, pol, acc, sbuf, tid);
+    else
+      piped_points<true>(ic, begin, end, pol, acc, sbuf, tid);
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -1517,11 +1563,21 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
   } else if (variant == 4 && !L.corr_out && !L.qkey_out) {
-    piped::linearize_piped_kernel<<<grid, piped::kThreads, 0, st>>>(L);
+    if (L.src_layout == kRows)
+      piped::linearize_piped_kernel<kRows><<<grid, piped::kThreads, 0, st>>>(L);
+    else if (L.src_layout == kBlocked)
+      piped::linearize_piped_kernel<kBlocked><<<grid, piped::kThreads, 0, st>>>(L);
+    else
+      piped::linearize_piped_kernel<kMixed><<<grid, piped::kThreads, 0, st>>>(L);
   } else if (variant == 4) {
     launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
-    compact::linearize_compact_kernel<<<grid, compact::kThreads, 0, st>>>(L);
+    if (L.src_layout == kRows)
+      compact::linearize_compact_kernel<kRows><<<grid, compact::kThreads, 0, st>>>(L);
+    else if (L.src_layout == kBlocked)
+      compact::linearize_compact_kernel<kBlocked><<<grid, compact::kThreads, 0, st>>>(L);
+    else
+      compact::linearize_compact_kernel<kMixed><<<grid, compact::kThreads, 0, st>>>(L);
   } else if (variant == 3) {
     launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
 
