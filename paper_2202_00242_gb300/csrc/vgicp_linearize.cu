@@ -833,6 +833,11 @@ __device__ __forceinline__ float4 lds_f4(const void* p) {
                : "r"((uint32_t)__cvta_generic_to_shared(p)));
   return v;
 }
+__device__ __forceinline__ uint64_t lds_u64(const void* p) {
+  uint64_t a;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return a;
+}
 __device__ __forceinline__ void lds_2ptr(const void* p, uint64_t& a, uint64_t& b) {
   asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
                : "=l"(a), "=l"(b)
@@ -850,9 +855,9 @@ __device__ __forceinline__ void simple_points(const LinLaunch& L, const ItemCons
   for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
     const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
     const float4 g3 = lds_f4(&ic.tmax);
-    uint64_t vs, ps, cs, pds;
+    uint64_t vs, ps, cs = 0;
     lds_2ptr(&ic.vslots, vs, ps);
-    lds_2ptr(&ic.covs, cs, pds);
+    if (!BLK) cs = lds_u64(&ic.covs);  // blocked sources need no covariance pointer
     Pose32 P;
     P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
     P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
@@ -864,7 +869,6 @@ __device__ __forceinline__ void simple_points(const LinLaunch& L, const ItemCons
     md.inv_r = g3.y;
     md.margin_scale = g3.z;
     const uint32_t mask = __float_as_uint(g3.w);
-    const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
 
     float x, y, z, c[6];
     load_point<BLK>(ps, cs, p, x, y, z, c);
@@ -885,7 +889,8 @@ __device__ __forceinline__ void simple_points(const LinLaunch& L, const ItemCons
       kx = clamp_to_int(fx);
       ky = clamp_to_int(fy);
       kz = clamp_to_int(fz);
-      if (ax | ay | az) {
+      if (ax | ay | az) {  // rare: the descriptor and r are read only here
+        const PairDesc* pd = ic.pd;
         MapDesc mr;
         mr.r = ic.r;
         if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
@@ -1181,259 +1186,6 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
 }
 }  // namespace compact
 
-// ---------------------------------------------------------------------------
-// Pipelined per-point kernel (1 neighbour, linearization).  The per-point
-// kernel waits, for every point, on the round trip of its voxel lookup, a load
-// that depends on the point's own load.  Here each thread computes the key of
-// its next point while the current one is evaluated and starts that key's
-// home-slot load as an asynchronous copy into its own 64 B of shared memory
-// (cp.async, 16-B chunks laid out [chunk][thread] so that both the copies and
-// the reads are conflict-free); when the thread reaches that point the slot is
-// usually there.  Probes past the home slot (rare) load synchronously.
-// ---------------------------------------------------------------------------
-namespace piped {
-constexpr int kThreads = kSimpleThreads;
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint64_t pol) {
-  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Exact key of source point p of the item's source (x, y, z loaded here).
-template <bool BLK>
-__device__ __forceinline__ void point_key(const ItemConst& icr, uint64_t ps, uint64_t cs,
-                                          int p, const Pose32& P, float inv_r,
-                                          float margin_scale, const PairDesc* pd, int& kx,
-                                          int& ky, int& kz) {
-  float x, y, z;
-  if (!BLK) {
-    const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
-    x = __ldg(pt + 0);
-    y = __ldg(pt + 1);
-    z = __ldg(pt + 2);
-  } else {
-    const float* g = blk_point(reinterpret_cast<const float*>(ps), p);
-    x = __ldg(g);
-    y = __ldg(g + 32);
-    z = __ldg(g + 64);
-  }
-  const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-  const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-  const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-  const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
-  const float m = fmaf(S, margin_scale, 1.1920928955078125e-7f);
-  const float yx = qx * inv_r, yy = qy * inv_r, yz = qz * inv_r;
-  const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-  const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-  const bool ax = (rx < m) | (rx > 1.0f - m);
-  const bool ay = (ry < m) | (ry > 1.0f - m);
-  const bool az = (rz < m) | (rz > 1.0f - m);
-  kx = clamp_to_int(fx);
-  ky = clamp_to_int(fy);
-  kz = clamp_to_int(fz);
-  if (ax | ay | az) {
-    MapDesc mr;
-    mr.r = icr.r;
-    if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-    if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-    if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-  }
-}
-
-// The item's constants from shared memory (see ItemConst).
-__device__ __forceinline__ void item_consts(const ItemConst& ic, Pose32& P, uint64_t& vs,
-                                            uint64_t& ps, uint64_t& cs, uint64_t& pds,
-                                            float& inv_r, float& margin, uint32_t& mask) {
-  const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-  const float4 g3 = lds_f4(&ic.tmax);
-  lds_2ptr(&ic.vslots, vs, ps);
-  lds_2ptr(&ic.covs, cs, pds);
-  P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
-  P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
-  P.R[8] = g2.x;
-  P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
-  P.tmax = g3.x;
-  inv_r = g3.y;
-  margin = g3.z;
-  mask = __float_as_uint(g3.w);
-}
-
-// The points of one work item (see the kernel); instantiated per source layout.
-template <bool BLK>
-__device__ __forceinline__ void piped_points(const ItemConst& ic, int begin, int end,
-                                             uint64_t pol, float (&acc)[kAcc],
-                                             uint4 (*sbuf)[4][kThreads], int tid) {
-  // the lookup state of the thread's current point (its home slot is in flight
-  // to, or has reached, sbuf[b])
-  unsigned long long key_c = kEmptyKey;
-  uint32_t h_c = 0;
-  int b = 0;
-  int p = begin + tid;
-  {
-    Pose32 P;
-    uint64_t vs, ps, cs, pds;
-    float inv_r, margin;
-    uint32_t mask;
-    item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
-    if (p < end) {
-      int kx, ky, kz;
-      point_key<BLK>(ic, ps, cs, p, P, inv_r, margin, reinterpret_cast<const PairDesc*>(pds), kx,
-                ky, kz);
-      if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
-        key_c = pack_key(kx, ky, kz);
-        h_c = hash_key(kx, ky, kz) & mask;
-        const char* src = reinterpret_cast<const char*>(reinterpret_cast<const VSlot*>(vs) + h_c);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cp_async16(&sbuf[0][c][tid], src + 16 * c, pol);
-      }
-    }
-    cp_async_commit();
-  }
-
-  for (; p < end; p += kThreads, b ^= 1) {
-    Pose32 P;
-    uint64_t vs, ps, cs, pds;
-    float inv_r, margin;
-    uint32_t mask;
-    item_consts(ic, P, vs, ps, cs, pds, inv_r, margin, mask);
-    const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
-    const VSlot* vslots = reinterpret_cast<const VSlot*>(vs);
-    // start the next point's lookup
-    unsigned long long key_n = kEmptyKey;
-    uint32_t h_n = 0;
-    const int pn = p + kThreads;
-    if (pn < end) {
-      int kx, ky, kz;
-      point_key<BLK>(ic, ps, cs, pn, P, inv_r, margin, pd, kx, ky, kz);
-      if (key_in_range(kx) && key_in_range(ky) && key_in_range(kz)) {
-        key_n = pack_key(kx, ky, kz);
-        h_n = hash_key(kx, ky, kz) & mask;
-        const char* src = reinterpret_cast<const char*>(vslots + h_n);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cp_async16(&sbuf[b ^ 1][c][tid], src + 16 * c, pol);
-      }
-    }
-    cp_async_commit();
-    // the current point
-    float x, y, z, c[6];
-    load_point<BLK>(ps, cs, p, x, y, z, c);
-    const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-    const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-    const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-    cp_async_wait<1>();  // this thread's copy of the current point's home slot
-    if (key_c != kEmptyKey) {
-      uint32_t a[8], bb[8];
-      {
-        const uint4 s0 = sbuf[b][0][tid], s1 = sbuf[b][1][tid];
-        const uint4 s2 = sbuf[b][2][tid], s3 = sbuf[b][3][tid];
-        a[0] = s0.x; a[1] = s0.y; a[2] = s0.z; a[3] = s0.w;
-        a[4] = s1.x; a[5] = s1.y; a[6] = s1.z; a[7] = s1.w;
-        bb[0] = s2.x; bb[1] = s2.y; bb[2] = s2.z; bb[3] = s2.w;
-        bb[4] = s3.x; bb[5] = s3.y; bb[6] = s3.z; bb[7] = s3.w;
-      }
-      unsigned long long t = slot_key(a);
-      if (t != key_c && t != kEmptyKey && a[7] != 0u) {  // probe on (rare)
-        uint32_t hh = h_c;
-        const int max_probe = ic.max_probe;
-        for (int q = 1; q < max_probe; ++q) {
-          hh = (hh + 1) & mask;
-          ld_v8(vslots + hh, pol, a);
-          ld_v8(reinterpret_cast<const char*>(vslots + hh) + 32, pol, bb);
-          t = slot_key(a);
-          if (t == key_c || t == kEmptyKey) break;
-        }
-      }
-      if (t == key_c) {
-        const float4 r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]),
-                                      __uint_as_float(a[6]), 0.f);
-        const float4 r1 = make_float4(__uint_as_float(bb[0]), __uint_as_float(bb[1]),
-                                      __uint_as_float(bb[2]), __uint_as_float(bb[3]));
-        const float4 r2 = make_float4(__uint_as_float(bb[4]), __uint_as_float(bb[5]), 0.f, 0.f);
-        add_term(acc, P, x, y, z, c, qx, qy, qz, r0, r1, r2);
-      }
-    }
-    key_c = key_n;
-    h_c = h_n;
-  }
-  cp_async_wait<0>();  // nothing in flight into sbuf when the next item starts
-}
-
-template <int LAYOUT>
-__global__ void __launch_bounds__(kThreads, VGICP_SIMPLE_MIN_BLOCKS)
-    linearize_piped_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ float red[kThreads / 32][kAcc];
-  __shared__ ItemConst ic;
-  __shared__ int next_item;
-  __shared__ __align__(16) uint4 sbuf[2][4][kThreads];  // [buffer][16-B chunk][thread]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-  const uint64_t pol = policy_evict_last_l();
-
-  for (int it = blockIdx.x; it < L.n_items;) {
-    int pair, begin, end;
-    tma::item_bounds(L, it, pair, begin, end);
-    if (threadIdx.x == 0) {
-      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) ic.R[k] = pd->R[k];
-      ic.t[0] = pd->t[0];
-      ic.t[1] = pd->t[1];
-      ic.t[2] = pd->t[2];
-      ic.tmax = pd->tmax;
-      ic.inv_r = md.inv_r;
-      ic.margin_scale = md.margin_scale;
-      ic.mask = *md.vmask;
-      ic.vslots = md.vslots;
-      ic.pts = sd.blk ? sd.blk : sd.pts;
-      ic.covs = sd.blk ? nullptr : sd.covs;
-      ic.pd = pd;
-      ic.r = md.r;
-      ic.max_probe = md.max_probe;
-    }
-    __syncthreads();
-
-    float acc[kAcc];
-#pragma unroll
-    for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
-
-    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
-      piped_points<false>(ic, begin, end, pol, acc, sbuf, tid);
-    else
-      piped_points<true>(ic, begin, end, pol, acc, sbuf, tid);
-
-#pragma unroll
-    for (int k = 0; k < kAcc; ++k) {
-      float v = acc[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-      acc[k] = v;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < kAcc; ++k) red[warp][k] = acc[k];
-    }
-    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
-    __syncthreads();
-    if (threadIdx.x < kAcc) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][threadIdx.x];
-      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
-    }
-    it = next_item;  // read between the two barriers; rewritten only after the second
-    __syncthreads();
-  }
-}
-}  // namespace piped
 
 
 // One warp per pair: lane k sums term k over the pair's items in order.  For the
@@ -1534,8 +1286,7 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  if (neighbours == 27 || variant == 1 || variant == 4)
-    return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
+  if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
   if (variant == 3) return device_sm_count() * VGICP_COMPACT_MIN_BLOCKS;
   return device_sm_count() * VGICP_MIN_BLOCKS;
 }
@@ -1562,15 +1313,6 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
-  } else if (variant == 4 && !L.corr_out && !L.qkey_out) {
-    if (L.src_layout == kRows)
-      piped::linearize_piped_kernel<kRows><<<grid, piped::kThreads, 0, st>>>(L);
-    else if (L.src_layout == kBlocked)
-      piped::linearize_piped_kernel<kBlocked><<<grid, piped::kThreads, 0, st>>>(L);
-    else
-      piped::linearize_piped_kernel<kMixed><<<grid, piped::kThreads, 0, st>>>(L);
-  } else if (variant == 4) {
-    launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
     if (L.src_layout == kRows)
       compact::linearize_compact_kernel<kRows><<<grid, compact::kThreads, 0, st>>>(L);
