@@ -437,8 +437,8 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   int item = opts && opts->tile > 0 ? opts->tile : 0;
@@ -532,8 +532,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -713,8 +713,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =

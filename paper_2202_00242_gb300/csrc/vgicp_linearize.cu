@@ -1186,6 +1186,200 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
 }
 }  // namespace compact
 
+// ---------------------------------------------------------------------------
+// Warp-staged per-point kernel (1 neighbour, linearization, blocked sources).
+// The per-point kernel with the stream taken off each point's dependency
+// chain: lane 0 of every warp copies the warp's next 32-point block (1,152 B,
+// contiguous in the blocked layout) into the warp's own double buffer in shared
+// memory with one bulk asynchronous copy (cp.async.bulk, completion on a
+// per-warp mbarrier) while the warp evaluates its current block.  No register
+// holds prefetched data and the copy does not pass through L1.  The waits are
+// bounded (2 s): a wait that runs out sets the status word (outputs NaN), the
+// warp stops staging and, before the kernel returns, waits (bounded) for its
+// copies in flight.
+// ---------------------------------------------------------------------------
+namespace wstage {
+constexpr int kThreads = kSimpleThreads;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kBlkBytes = kBlkFloats * 4;
+
+// Orders this thread's earlier shared-memory accesses before later asynchronous
+// (bulk copy) writes to shared memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__global__ void __launch_bounds__(kThreads, VGICP_SIMPLE_MIN_BLOCKS)
+    linearize_wstage_kernel(const __grid_constant__ LinLaunch L) {
+  __shared__ float red[kWarps][kAcc];
+  __shared__ ItemConst ic;
+  __shared__ int next_item;
+  __shared__ __align__(128) float stage[kWarps][2][kBlkFloats];
+  __shared__ uint64_t bar[kWarps][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol = policy_evict_last_l();
+  const uint64_t spol = policy_evict_normal();
+  if (lane == 0) {
+    mbar_init(&bar[warp][0], 1);
+    mbar_init(&bar[warp][1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t u = 0;         // blocks this warp has consumed (block u is in stage u & 1)
+  uint32_t issued = 0;    // blocks this warp has staged
+  bool dead = false;      // a wait ran out: stop staging
+  uint32_t dead_from = 0; // then blocks [dead_from, issued) may still be in flight
+
+  for (int it = blockIdx.x; it < L.n_items;) {
+    int pair, begin, end;
+    tma::item_bounds(L, it, pair, begin, end);
+    if (threadIdx.x == 0) {
+      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
+      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
+      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) ic.R[k] = pd->R[k];
+      ic.t[0] = pd->t[0];
+      ic.t[1] = pd->t[1];
+      ic.t[2] = pd->t[2];
+      ic.tmax = pd->tmax;
+      ic.inv_r = md.inv_r;
+      ic.margin_scale = md.margin_scale;
+      ic.mask = *md.vmask;
+      ic.vslots = md.vslots;
+      ic.pts = sd.blk;  // blocked sources only
+      ic.covs = nullptr;
+      ic.pd = pd;
+      ic.r = md.r;
+      ic.max_probe = md.max_probe;
+    }
+    __syncthreads();
+
+    float acc[kAcc];
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
+
+    const float* blk = ic.pts;
+    int p0 = begin + kBlkPts * warp;  // the warp's first block of the item
+    if (!dead && p0 < end) {
+      if (lane == 0) {
+        uint64_t* b = &bar[warp][issued & 1];
+        fence_proxy_async();
+        mbar_arrive_expect_tx(b, kBlkBytes);
+        bulk_g2s(stage[warp][issued & 1], blk + (int64_t)(p0 / kBlkPts) * kBlkFloats, kBlkBytes,
+                 b, spol);
+      }
+      ++issued;
+    }
+    for (; p0 < end; p0 += kThreads, ++u) {  // warp-uniform
+      const int s = u & 1;
+      const int pn = p0 + kThreads;
+      if (!dead && pn < end) {  // the next block into the other buffer (read last round)
+        if (lane == 0) {
+          uint64_t* b = &bar[warp][issued & 1];
+          fence_proxy_async();  // this warp's reads of that buffer before the copy's writes
+          mbar_arrive_expect_tx(b, kBlkBytes);
+          bulk_g2s(stage[warp][issued & 1], blk + (int64_t)(pn / kBlkPts) * kBlkFloats,
+                   kBlkBytes, b, spol);
+        }
+        ++issued;
+      }
+      bool ok = dead || mbar_wait(&bar[warp][s], (u >> 1) & 1);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok && !dead) {
+        if (lane == 0) atomicExch(L.status, 1);
+        dead = true;
+        dead_from = u;
+      }
+      if (dead) continue;
+      const int p = p0 + lane;
+      float x = 0.f, y = 0.f, z = 0.f, c[6];
+      if (p < end) {
+        const float* g = stage[warp][s] + lane;
+        x = g[0];
+        y = g[32];
+        z = g[64];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] = g[96 + 32 * k];
+      }
+      __syncwarp();  // every lane has read stage s before it is refilled
+      if (p >= end) continue;
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float4 g3 = lds_f4(&ic.tmax);
+      Pose32 P;
+      P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
+      P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
+      P.R[8] = g2.x;
+      P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
+      P.tmax = g3.x;
+      const float inv_r = g3.y, margin = g3.z;
+      const uint32_t mask = __float_as_uint(g3.w);
+      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+      int kx, ky, kz;
+      {
+        const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
+        const float m = fmaf(S, margin, 1.1920928955078125e-7f);
+        const float yx = qx * inv_r, yy = qy * inv_r, yz = qz * inv_r;
+        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+        const bool ax = (rx < m) | (rx > 1.0f - m);
+        const bool ay = (ry < m) | (ry > 1.0f - m);
+        const bool az = (rz < m) | (rz > 1.0f - m);
+        kx = clamp_to_int(fx);
+        ky = clamp_to_int(fy);
+        kz = clamp_to_int(fz);
+        if (ax | ay | az) {  // rare: the descriptor and r are read only here
+          const PairDesc* pd = ic.pd;
+          MapDesc mr;
+          mr.r = ic.r;
+          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+        }
+      }
+      MapDesc md;
+      md.vslots = ic.vslots;
+      md.max_probe = ic.max_probe;
+      float4 a0, a1, a2;
+      const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+      if (vid >= 0) add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+    }
+
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) {
+      float v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      acc[k] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kAcc; ++k) red[warp][k] = acc[k];
+    }
+    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
+    __syncthreads();
+    if (threadIdx.x < kAcc) {
+      double s = 0.0;
+      for (int w = 0; w < kWarps; ++w) s += (double)red[w][threadIdx.x];
+      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
+    }
+    it = next_item;  // read between the two barriers; rewritten only after the second
+    __syncthreads();
+  }
+  if (dead && lane == 0) {
+    // let this warp's copies in flight land before the block exits
+    for (uint32_t v = dead_from; v < issued; ++v) mbar_wait(&bar[warp][v & 1], (v >> 1) & 1);
+  }
+}
+}  // namespace wstage
+
 
 
 // One warp per pair: lane k sums term k over the pair's items in order.  For the
@@ -1286,7 +1480,8 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
+  if (neighbours == 27 || variant == 1 || variant == 4)
+    return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
   if (variant == 3) return device_sm_count() * VGICP_COMPACT_MIN_BLOCKS;
   return device_sm_count() * VGICP_MIN_BLOCKS;
 }
@@ -1313,6 +1508,10 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
+  } else if (variant == 4 && L.src_layout == kBlocked && L.neighbours == 1) {
+    wstage::linearize_wstage_kernel<<<grid, wstage::kThreads, 0, st>>>(L);
+  } else if (variant == 4) {
+    launch_simple<1, 0>(L, grid, st);  // the warp-staged kernel reads blocked sources only
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
     if (L.src_layout == kRows)
       compact::linearize_compact_kernel<kRows><<<grid, compact::kThreads, 0, st>>>(L);

@@ -240,8 +240,8 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 3))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (opts && (opts->variant < 0 || opts->variant > 4))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
   if (opts && opts->tile > 0 && opts->tile < kMinItem)
@@ -365,7 +365,7 @@ int vgicp_plan_autotune(vgicp_plan* P, const double* poses, vgicp_stream_t strea
   rc = upload_poses(P, buf, st);
   if (rc) return rc;
   VGICP_CUDA_TRY(cudaStreamSynchronize(st));
-  const int variants_1[] = {1, 2, 3};
+  const int variants_1[] = {1, 2, 3, 4};
   const int variants_27[] = {1};
   const int* vs = P->neighbours == 27 ? variants_27 : variants_1;
   const int nv = P->neighbours == 27 ? 1 : (int)(sizeof(variants_1) / sizeof(variants_1[0]));
