@@ -201,7 +201,7 @@ __device__ __forceinline__ void insert_lookup(uint32_t v, unsigned long long key
   const int kz = (int)(key & fm) - kKeyBias;
   const uint32_t mask = vmask[lo];
   VSlot* t = vslots + slot_base[lo];
-  const uint32_t home = hash_key(kx, ky, kz) & mask;
+  const uint32_t home = lookup_home(kx, ky, kz) & mask;
   uint32_t h = home;
   bool placed = false;
   for (int p = 0; p < max_probe; ++p) {

@@ -142,6 +142,16 @@ __device__ __forceinline__ uint32_t hash_key(int kx, int ky, int kz) {
   return h ^ (h >> 16);
 }
 
+// Home slot (before the capacity mask) of a voxel in a lookup table: the 2x2x2
+// block of voxels (k >> 1 per axis, floor for negative k) is hashed to a run of
+// 8 consecutive slots and the voxel takes the slot of its position in the block.
+// Neighbouring voxels thus share 128-B lines, and the lookups of a warp's
+// spatially close points, and of the next warps', hit the same few lines in L1.
+__device__ __forceinline__ uint32_t lookup_home(int kx, int ky, int kz) {
+  return (hash_key(kx >> 1, ky >> 1, kz >> 1) << 3) |
+         (uint32_t)((kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2));
+}
+
 // Clamp a float to the int range before conversion, so out-of-range values map
 // to out-of-range keys instead of wrapping.
 __device__ __forceinline__ int clamp_to_int(float f) {

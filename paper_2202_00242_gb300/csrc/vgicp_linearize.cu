@@ -131,7 +131,7 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
                                       uint64_t pol, float4& r0, float4& r1, float4& r2) {
   if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) return -1;
   const unsigned long long key = pack_key(kx, ky, kz);
-  uint32_t h = hash_key(kx, ky, kz) & mask;
+  uint32_t h = lookup_home(kx, ky, kz) & mask;
   for (int p = 0; p < md.max_probe; ++p) {
     uint32_t a[8], b[8];
     const VSlot* t = md.vslots + h;
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
         live[k] = key_in_range(kx[k]) && key_in_range(ky[k]) && key_in_range(kz[k]);
       }
       key[k] = live[k] ? pack_key(kx[k], ky[k], kz[k]) : kEmptyKey;
-      h[k] = hash_key(kx[k], ky[k], kz[k]) & mask;
+      h[k] = lookup_home(kx[k], ky[k], kz[k]) & mask;
       if (live[k]) {
         ld_v8(md.vslots + h[k], map_pol, sa[k]);
         ld_v8(reinterpret_cast<const char*>(md.vslots + h[k]) + 32, map_pol, sb[k]);
