@@ -20,9 +20,8 @@ int64_t vgicp_voxelmap_bytes(int64_t n_points, const vgicp_map_opts* opts) {
   int64_t cap = 16, vcap = 16;
   while (cap < std::max<int64_t>(n_points, 1) * cf) cap <<= 1;
   while (vcap < std::max<int64_t>(n_points, 8) * (int64_t)vgicp::kLookupLoad) vcap <<= 1;
-  // build table + lookup table + records + keys + grouped cloud (with its last
-  // block padded to 32 points) + scratch
-  return cap * 16 + vcap * 64 + n_points * (48 + 8 + 36 + 4 * 9) + 9 * 32 * 4 + 4096;
+  // build table + lookup table + records + keys + grouped cloud + scratch
+  return cap * 16 + vcap * 64 + n_points * (48 + 8 + 36 + 4 * 9) + 4096;
 }
 
 int vgicp_admission_schedule(const int64_t* map_bytes, int32_t n_maps, const int64_t* src_bytes,

@@ -32,12 +32,6 @@ uint32_t next_pow2(uint64_t x) {
 
 bool finite_pose(const double* T) { return se3::rigid(T); }
 
-int sources_layout(const SrcDesc* sd, size_t n) {
-  size_t blocked = 0;
-  for (size_t i = 0; i < n; ++i) blocked += sd[i].blk ? 1 : 0;
-  return blocked == 0 ? kRows : blocked == n ? kBlocked : kMixed;
-}
-
 PairDesc make_pair_desc(const double* T, int32_t map, int32_t src) {
   return se3::pair_desc(T, map, src);
 }
@@ -143,13 +137,8 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->n_chunks = (int32_t)chunks.size();
   const size_t o_chunks = take(sizeof(int2) * chunks.size());
   const size_t o_goff = take(sizeof(uint32_t) * n);
-  s->gblk_off.assign((size_t)n_maps + 1, 0);
-  for (int32_t m = 0; m < n_maps; ++m) {
-    const int64_t nm = offsets[m + 1] - offsets[m];
-    s->gblk_off[(size_t)m + 1] = s->gblk_off[(size_t)m] + (nm + kBlkPts - 1) / kBlkPts;
-  }
-  const size_t o_gblk = take(sizeof(float) * kBlkFloats * (size_t)s->gblk_off[(size_t)n_maps]);
-  const size_t o_gblk_off = take(sizeof(int64_t) * (n_maps + 1));
+  const size_t o_gpts = take(sizeof(float) * 3 * n);
+  const size_t o_gcovs = take(sizeof(float) * 6 * n);
   const size_t o_scan = take(sizeof(uint32_t) * s->scan_tmp_elems);
   cudaError_t e = device_malloc(&s->d_block, off, nullptr, false);
   if (e != cudaSuccess) {
@@ -179,10 +168,10 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->d_plist = reinterpret_cast<uint32_t*>(b + o_plist);
   s->d_vslot_of = reinterpret_cast<uint32_t*>(b + o_vslot_of);
   s->d_lslot_of = reinterpret_cast<uint32_t*>(b + o_lslot_of);
-  s->d_gblk = reinterpret_cast<float*>(b + o_gblk);
-  s->d_gblk_off = reinterpret_cast<int64_t*>(b + o_gblk_off);
+  s->d_gpts = reinterpret_cast<float*>(b + o_gpts);
   s->d_goff = reinterpret_cast<uint32_t*>(b + o_goff);
   s->d_chunks = reinterpret_cast<int2*>(b + o_chunks);
+  s->d_gcovs = reinterpret_cast<float*>(b + o_gcovs);
   s->d_scan_tmp = reinterpret_cast<uint32_t*>(b + o_scan);
   cudaGetDevice(&s->device);
   std::vector<uint32_t> mask(n_maps);
@@ -198,13 +187,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   if (e == cudaSuccess)
     e = cudaMemcpy(s->d_chunks, chunks.data(), sizeof(int2) * chunks.size(),
                    cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(s->d_gblk_off, s->gblk_off.data(), sizeof(int64_t) * (n_maps + 1),
-                   cudaMemcpyHostToDevice);
-  // the padding of each map's last block is never read as a point, but is kept
-  // defined (zero)
-  if (e == cudaSuccess && s->gblk_off[(size_t)n_maps] > 0)
-    e = cudaMemset(s->d_gblk, 0, sizeof(float) * kBlkFloats * (size_t)s->gblk_off[(size_t)n_maps]);
   if (e != cudaSuccess) {
     free_set(s);
     return check_cuda(e, "cudaMemcpy(map metadata)");
@@ -437,8 +419,8 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   int item = opts && opts->tile > 0 ? opts->tile : 0;
@@ -459,7 +441,7 @@ int vgicp_linearize(const vgicp_map* map, const float* src_points, const float* 
   L.item_size = item;
   L.single = make_pair_desc(T_target_source, 0, 0);
   L.single_map = make_map_desc(map);
-  L.single_src = SrcDesc{src_points, src_covs, n_src, nullptr};
+  L.single_src = SrcDesc{src_points, src_covs, n_src};
   L.corr_out = opts ? opts->corr_out : nullptr;
   L.qkey_out = opts ? opts->qkey_out : nullptr;
   L.neighbours = neighbours;
@@ -532,8 +514,8 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   for (int32_t m = 0; m < n_maps; ++m)
     if (!maps[m]) return set_error(VGICP_ERR_INVALID_ARG, "null map handle");
   // resolve sources: user clouds, or a map's own voxel-grouped cloud
@@ -543,18 +525,14 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
       const vgicp_map* m = sources[c].map;
       const MapSet* ms = m->set;
       const int64_t a = ms->point_off[m->index], b = ms->point_off[m->index + 1];
-      sd[(size_t)c] = SrcDesc{nullptr, nullptr, b - a,
-                              ms->d_gblk + kBlkFloats * ms->gblk_off[(size_t)m->index]};
+      sd[(size_t)c] = SrcDesc{ms->d_gpts + 3 * a, ms->d_gcovs + 6 * a, b - a};
     } else {
       int rc = check_cloud(sources[c].points, sources[c].covs, sources[c].n, "source cloud");
       if (rc) return rc;
-      sd[(size_t)c] = SrcDesc{sources[c].points, sources[c].covs, sources[c].n, nullptr};
+      sd[(size_t)c] = SrcDesc{sources[c].points, sources[c].covs, sources[c].n};
     }
   }
-  // work items start on 32-point blocks of the sources (the blocked layout of
-  // maps' grouped copies; the staged kernel copies whole blocks)
-  const int item = opts && opts->tile > 0 ? (opts->tile + kBlkPts - 1) / kBlkPts * kBlkPts
-                                          : default_item_size();
+  const int item = opts && opts->tile > 0 ? opts->tile : default_item_size();
   // host planner: pair descriptors; work items (chunks of each pair's source),
   // emitted in order of (target map, source) so that concurrently running CTAs
   // share a few target maps in L2; span[p] = the items of pair p.
@@ -634,7 +612,6 @@ static int batched_impl(vgicp_map* const* maps, int32_t n_maps, const vgicp_clou
     L.pairs = reinterpret_cast<const PairDesc*>(dev + o_pd);
     L.maps = reinterpret_cast<const MapDesc*>(dev + o_md);
     L.srcs = reinterpret_cast<const SrcDesc*>(dev + o_sd);
-    L.src_layout = sources_layout(sd.data(), sd.size());
     L.partials = reinterpret_cast<double*>(dev + o_part);
     L.status = reinterpret_cast<int32_t*>(dev + o_status);
     L.neighbours = neighbours;
@@ -713,8 +690,8 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   int item = opts && opts->tile > 0 ? opts->tile : 0;
   if (item == 0) {
     const int64_t target_items =
@@ -743,7 +720,7 @@ extern "C" int vgicp_linearize_noalloc(const vgicp_map* map, const float* src_po
   L.item_size = item;
   L.single = make_pair_desc(T_target_source, 0, 0);
   L.single_map = make_map_desc(map);
-  L.single_src = SrcDesc{src_points, src_covs, n_src, nullptr};
+  L.single_src = SrcDesc{src_points, src_covs, n_src};
   L.corr_out = opts ? opts->corr_out : nullptr;
   L.qkey_out = opts ? opts->qkey_out : nullptr;
   L.neighbours = neighbours;

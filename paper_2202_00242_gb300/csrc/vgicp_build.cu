@@ -201,7 +201,7 @@ __device__ __forceinline__ void insert_lookup(uint32_t v, unsigned long long key
   const int kz = (int)(key & fm) - kKeyBias;
   const uint32_t mask = vmask[lo];
   VSlot* t = vslots + slot_base[lo];
-  const uint32_t home = lookup_home(kx, ky, kz) & mask;
+  const uint32_t home = hash_key(kx, ky, kz) & mask;
   uint32_t h = home;
   bool placed = false;
   for (int p = 0; p < max_probe; ++p) {
@@ -268,40 +268,16 @@ __device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
   }
 }
 
-// Map of rank (or voxel id) r: the last m with vbase[m] <= r.
-__device__ __forceinline__ int map_of_rank(const uint32_t* __restrict__ vbase, int32_t n_maps,
-                                           int64_t r) {
-  int lo = 0, hi = n_maps;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if ((int64_t)vbase[mid] <= r) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Index in the blocked grouped copy of grouped position d of map m: the map's
-// copy starts on block gblk_off[m]; its grouped positions start at the list
-// offset of its first rank.
-__device__ __forceinline__ int64_t blocked_index(int64_t d, int m,
-                                                 const uint32_t* __restrict__ vbase,
-                                                 const uint32_t* __restrict__ goff,
-                                                 const int64_t* __restrict__ gblk_off, int64_t V,
-                                                 uint32_t total) {
-  const int64_t first = (int64_t)vbase[m] < V ? (int64_t)goff[vbase[m]] : (int64_t)total;
-  return d - first + kBlkPts * gblk_off[m];
-}
-
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     int64_t n_max, const uint32_t* __restrict__ n_vox, const uint32_t* __restrict__ n_valid,
     const float* __restrict__ pts, const float* __restrict__ covs,
     const uint32_t* __restrict__ vorder, const uint32_t* __restrict__ goff,
-    uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gblk,
-    const int64_t* __restrict__ gblk_off, const unsigned long long* __restrict__ vkeys,
-    int32_t n_maps, const uint32_t* __restrict__ vbase, const int64_t* __restrict__ slot_base,
+    uint32_t* __restrict__ plist, float4* __restrict__ recs, float* gpts, float* gcovs,
+    const unsigned long long* __restrict__ vkeys, int32_t n_maps,
+    const uint32_t* __restrict__ vbase, const int64_t* __restrict__ slot_base,
     const uint32_t* __restrict__ vmask, int32_t max_probe, VSlot* vslots,
     uint32_t* __restrict__ lslot_of, int32_t* status) {
   __shared__ uint32_t stage[kFinStage];
-  __shared__ int seg_maps[2];
   const int64_t V = min((int64_t)*n_vox, n_max);
   const uint32_t total = *n_valid;  // end of the last list (goff[V] is not stored)
   for (int64_t r0 = (int64_t)blockIdx.x * kFinThreads; r0 < V; r0 += (int64_t)gridDim.x * kFinThreads) {
@@ -316,10 +292,6 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     const uint32_t v = mine ? vorder[r] : 0u;
     const uint32_t o = mine ? goff[r] : 0u;
     const uint32_t c = mine ? (r + 1 < V ? goff[r + 1] : total) - o : 0u;
-    if (threadIdx.x == 0) {  // the maps of the CTA's first and last ranks
-      seg_maps[0] = map_of_rank(vbase, n_maps, r0);
-      seg_maps[1] = map_of_rank(vbase, n_maps, r1 - 1);
-    }
     // 1. sort the lists by point index
     if (staged) {
       for (uint32_t i = threadIdx.x; i < len; i += kFinThreads) stage[i] = plist[seg0 + i];
@@ -329,29 +301,21 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
       insertion_sort(plist + o, c);
     }
     __syncthreads();
-    // 2. gather into the grouped cloud (blocked: consecutive positions are
-    // consecutive floats of each component array, so the writes coalesce)
+    // 2. gather into the grouped cloud
     const uint32_t* lst = staged ? stage : plist + seg0;
-    const int ma = seg_maps[0], mb = seg_maps[1];
     for (uint32_t i = threadIdx.x; i < len; i += kFinThreads) {
       const int64_t j = lst[i];
       const float x = __ldg(pts + 3 * j), y = __ldg(pts + 3 * j + 1), z = __ldg(pts + 3 * j + 2);
       const float2* cv = reinterpret_cast<const float2*>(covs + 6 * j);
       const float2 c0 = __ldg(cv), c1 = __ldg(cv + 1), c2 = __ldg(cv + 2);
       const int64_t d = (int64_t)seg0 + i;
-      int m = ma;  // the map whose grouped positions hold d (a CTA rarely spans two)
-      while (m < mb && (int64_t)vbase[m + 1] < V && d >= (int64_t)goff[vbase[m + 1]]) ++m;
-      const int64_t q = blocked_index(d, m, vbase, goff, gblk_off, V, total);
-      float* g = gblk + (q >> 5) * kBlkFloats + (q & 31);
-      g[0] = x;
-      g[32] = y;
-      g[64] = z;
-      g[96] = c0.x;
-      g[128] = c0.y;
-      g[160] = c1.x;
-      g[192] = c1.y;
-      g[224] = c2.x;
-      g[256] = c2.y;
+      gpts[3 * d + 0] = x;
+      gpts[3 * d + 1] = y;
+      gpts[3 * d + 2] = z;
+      float2* gc = reinterpret_cast<float2*>(gcovs + 6 * d);
+      gc[0] = c0;
+      gc[1] = c1;
+      gc[2] = c2;
     }
     __syncthreads();  // the CTA's global writes are visible to the CTA after this
     // 3. sums from the grouped copy (plain loads: written by this kernel)
@@ -360,14 +324,14 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
 #pragma unroll
       for (int k = 0; k < 9; ++k) hi[k] = lo[k] = 0.0f;
       bool exact = true;
-      const int mv = map_of_rank(vbase, n_maps, r);
-      const int64_t q0 = blocked_index((int64_t)o, mv, vbase, goff, gblk_off, V, total);
       for (uint32_t a = 0; a < c; ++a) {
-        const int64_t q = q0 + a;
-        const float* g = gblk + (q >> 5) * kBlkFloats + (q & 31);
+        const int64_t d = (int64_t)o + a;
         float f[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) f[k] = g[32 * k];
+        for (int k = 0; k < 3; ++k) f[k] = gpts[3 * d + k];
+        const float2* gc = reinterpret_cast<const float2*>(gcovs + 6 * d);
+        const float2 c0 = gc[0], c1 = gc[1], c2 = gc[2];
+        f[3] = c0.x; f[4] = c0.y; f[5] = c1.x; f[6] = c1.y; f[7] = c2.x; f[8] = c2.y;
         // hi + lo stays the exact sum while each TwoSum error adds exactly to lo
         // (checked); renormalised once at the end
 #pragma unroll
@@ -411,10 +375,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
 #pragma unroll
           for (int k = 0; k < 9; ++k) sum[k] = 0.0;
           for (uint32_t a = 0; a < c; ++a) {
-            const int64_t q = q0 + a;
-            const float* g = gblk + (q >> 5) * kBlkFloats + (q & 31);
+            const int64_t d = (int64_t)o + a;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) sum[k] = __dadd_rn(sum[k], (double)g[32 * k]);
+            for (int k = 0; k < 3; ++k) sum[k] = __dadd_rn(sum[k], (double)gpts[3 * d + k]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sum[3 + k] = __dadd_rn(sum[3 + k], (double)gcovs[6 * d + k]);
           }
         }
         const double N = (double)c;
@@ -942,7 +907,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   // sums, records, grouped clouds and the lookup tables
   finalize_kernel<<<g, kFinThreads, 0, st>>>(
       n, s->d_num_voxels, s->d_num_valid, points, covs, vorder, s->d_goff, s->d_plist, s->d_recs,
-      s->d_gblk, s->d_gblk_off, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
+      s->d_gpts, s->d_gcovs, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
       s->max_probe, s->d_vslots, s->d_lslot_of, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
   // insert, vbase, sort, scatter, vslot init, finalize (+ reset or init: 1; the two

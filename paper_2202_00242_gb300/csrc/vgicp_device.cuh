@@ -85,26 +85,11 @@ struct PairDesc {
   double t64[3];
 };
 
-// A source cloud: the caller's rows (pts n x 3, covs n x 6), or, when blk is
-// set, a map's voxel-grouped copy in 32-point blocks (see kBlkFloats).
 struct SrcDesc {
-  const float* pts;   // n x 3 (rows)
-  const float* covs;  // n x 6 (rows)
+  const float* pts;   // n x 3
+  const float* covs;  // n x 6
   int64_t n;
-  const float* blk;   // non-null: blocked layout (pts and covs unused)
 };
-
-// Blocked layout of the voxel-grouped copy of a map's cloud: blocks of 32
-// consecutive points, each block 9 arrays of 32 floats (x, y, z, then the
-// covariance entries xx xy xz yy yz zz).  Point p of a map is component k at
-// blk[(p / 32) * kBlkFloats + 32 k + p % 32]; the 32 lanes of a warp reading 32
-// consecutive points read one 128-B line per component.  Each map's copy starts
-// on a block; the tail of its last block is padding.
-constexpr int kBlkPts = 32;
-constexpr int kBlkFloats = 9 * kBlkPts;
-__device__ __forceinline__ const float* blk_point(const float* blk, int64_t p) {
-  return blk + (p >> 5) * kBlkFloats + (p & 31);
-}
 
 // Voxels of a map are put in Morton order in chunks of this many (one CTA sorts
 // one chunk in shared memory).
@@ -140,16 +125,6 @@ __device__ __forceinline__ bool key_in_range(int k) { return k >= kKeyMin && k <
 __device__ __forceinline__ uint32_t hash_key(int kx, int ky, int kz) {
   uint32_t h = (uint32_t)kx * 0x8DA6B343u + (uint32_t)ky * 0xD8163841u + (uint32_t)kz * 0xCB1AB31Fu;
   return h ^ (h >> 16);
-}
-
-// Home slot (before the capacity mask) of a voxel in a lookup table: the 2x2x2
-// block of voxels (k >> 1 per axis, floor for negative k) is hashed to a run of
-// 8 consecutive slots and the voxel takes the slot of its position in the block.
-// Neighbouring voxels thus share 128-B lines, and the lookups of a warp's
-// spatially close points, and of the next warps', hit the same few lines in L1.
-__device__ __forceinline__ uint32_t lookup_home(int kx, int ky, int kz) {
-  return (hash_key(kx >> 1, ky >> 1, kz >> 1) << 3) |
-         (uint32_t)((kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2));
 }
 
 // Clamp a float to the int range before conversion, so out-of-range values map

@@ -70,12 +70,8 @@ struct MapSet {
   uint32_t* d_lslot_of = nullptr; // n_total: lookup-table slot of each voxel (or kNoSlot)
   bool built = false;             // a build has run: the lookup tables hold only its
                                   // voxels and the build table is empty
-  // the clouds grouped by voxel (voxels in Morton order within chunks of a map,
-  // each voxel's points in index order), in 32-point blocks (kBlkFloats); map m's
-  // copy is blocks [gblk_off[m], gblk_off[m + 1])
-  float* d_gblk = nullptr;
-  std::vector<int64_t> gblk_off;  // n_maps + 1, in blocks
-  int64_t* d_gblk_off = nullptr;  // the same on the device
+  float* d_gpts = nullptr;        // n_total x 3: the clouds grouped by voxel, voxels in
+  float* d_gcovs = nullptr;       // n_total x 6   Morton order (within chunks of a map)
   uint32_t* d_goff = nullptr;     // n_total: grouped offset of each Morton rank
   int2* d_chunks = nullptr;       // (map, chunk) pairs for the Morton sort
   int32_t n_chunks = 0;
@@ -110,10 +106,6 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_max,
 size_t scan_tmp_elems(int64_t n_max);
 
 // ---- kernels (vgicp_linearize.cu) ----------------------------------------
-constexpr int kRows = 0, kBlocked = 1, kMixed = 2;  // source layouts of a launch
-// The layout of a set of sources (kRows for none).
-int sources_layout(const SrcDesc* sd, size_t n);
-
 struct LinLaunch {
   const WorkItem* items;     // null: uniform items of pair 0 (single factor)
   int32_t n_items;
@@ -136,8 +128,6 @@ struct LinLaunch {
   int32_t grid;              // 0 = automatic
   cudaEvent_t ev_start;      // optional, recorded around the kernel
   cudaEvent_t ev_stop;
-  int32_t src_layout;        // kRows: every source is the caller's rows; kBlocked: every
-                             // source is a map's blocked copy; kMixed: both
   int64_t wait_limit_ns;     // staged kernel: bound of its mbarrier waits (0 = 2 s)
   int32_t test_withhold_tile;  // staged kernel, tests only: 1 + the tile index each
                                // producer withholds (0 = none)

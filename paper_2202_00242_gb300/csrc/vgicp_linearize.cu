@@ -131,7 +131,7 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
                                       uint64_t pol, float4& r0, float4& r1, float4& r2) {
   if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) return -1;
   const unsigned long long key = pack_key(kx, ky, kz);
-  uint32_t h = lookup_home(kx, ky, kz) & mask;
+  uint32_t h = hash_key(kx, ky, kz) & mask;
   for (int p = 0; p < md.max_probe; ++p) {
     uint32_t a[8], b[8];
     const VSlot* t = md.vslots + h;
@@ -365,49 +365,16 @@ struct TileDesc {
   int32_t pair, begin, n, item, flags, xyz_off, cov_off, pad;
 };
 
-constexpr int kBlocked = 4;  // TileDesc flag: the tile is whole 32-point blocks
-
-// Stage s holds a tile of the caller's rows (coordinates at buf[s], covariances
-// at buf[s] + kXyzBytes) or kTile / 32 blocks of a blocked source at buf[s].
 struct __align__(16) Smem {
   float4 hits[kNCW][kWarpPts * 3];            // staged voxel records of hits
-  unsigned char buf[kStages][kXyzBytes + kCovBytes];
+  unsigned char xyz[kStages][kXyzBytes];
+  unsigned char cov[kStages][kCovBytes];
   TileDesc desc[kStages];
   uint64_t full[kStages];
   uint64_t empty[kStages];
   float red[kNCW][32];
 };
 static_assert(kXyzBytes % 16 == 0 && kCovBytes % 16 == 0, "bulk-copy alignment");
-static_assert(kTile % kBlkPts == 0 && (kTile / kBlkPts) * kBlkFloats * 4 <= kXyzBytes + kCovBytes,
-              "a tile of blocks fits a stage");
-
-// Point i of a staged tile: x, y, z and the covariance (blocked or rows).
-__device__ __forceinline__ void tile_point(const unsigned char* buf, const TileDesc& d, int i,
-                                           float& x, float& y, float& z) {
-  if (d.flags & kBlocked) {
-    const float* g = blk_point(reinterpret_cast<const float*>(buf), i);
-    x = g[0];
-    y = g[32];
-    z = g[64];
-  } else {
-    const float* X = reinterpret_cast<const float*>(buf + d.xyz_off);
-    x = X[3 * i];
-    y = X[3 * i + 1];
-    z = X[3 * i + 2];
-  }
-}
-__device__ __forceinline__ void tile_cov(const unsigned char* buf, const TileDesc& d, int i,
-                                         float* c) {
-  if (d.flags & kBlocked) {
-    const float* g = blk_point(reinterpret_cast<const float*>(buf), i);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c[k] = g[96 + 32 * k];
-  } else {
-    const float2* cv = reinterpret_cast<const float2*>(buf + kXyzBytes + d.cov_off + 24 * i);
-    const float2 c01 = cv[0], c23 = cv[1], c45 = cv[2];
-    c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y; c[4] = c45.x; c[5] = c45.y;
-  }
-}
 
 // Copy the float range [gs, ge) of global memory into shared memory at
 // dst + (gs - floor16(gs)): the 16-B aligned interior with one bulk copy
@@ -501,41 +468,26 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
           break;
         }
         const int n = min(kTile, e - t0);
+        const uintptr_t xs = reinterpret_cast<uintptr_t>(sd.pts + 3 * (int64_t)t0);
+        const uintptr_t cs = reinterpret_cast<uintptr_t>(sd.covs + 6 * (int64_t)t0);
+        // head/tail cp.async and the descriptor, then the two arrivals, then bulk
+        const uintptr_t xe = xs + 12 * (uintptr_t)n, ce = cs + 24 * (uintptr_t)n;
+        const uint32_t tx = stage_range(S.xyz[s], xs, xe, &S.full[s], false, stream_pol) +
+                            stage_range(S.cov[s], cs, ce, &S.full[s], false, stream_pol);
         TileDesc d;
         d.pair = pair;
         d.begin = t0;
         d.n = n;
         d.item = it;
         d.flags = (t0 == b ? kFirst : 0) | (t0 + kTile >= e ? kLast : 0);
+        d.xyz_off = (int)(xs & 15);
+        d.cov_off = (int)(cs & 15);
         d.pad = 0;
-        if (sd.blk) {
-          // whole blocks: items and tiles start on a block, and the last block of
-          // a map's copy is allocated in full (its tail is padding)
-          const uint32_t bytes = (uint32_t)((n + kBlkPts - 1) / kBlkPts) * kBlkFloats * 4;
-          d.flags |= kBlocked;
-          d.xyz_off = d.cov_off = 0;
-          S.desc[s] = d;
-          cp_async_arrive_noinc(&S.full[s]);
-          mbar_arrive_expect_tx(&S.full[s], bytes);
-          bulk_g2s(S.buf[s], sd.blk + (int64_t)(t0 / kBlkPts) * kBlkFloats, bytes, &S.full[s],
-                   stream_pol);
-        } else {
-          unsigned char* sx = S.buf[s];
-          unsigned char* sc = S.buf[s] + kXyzBytes;
-          const uintptr_t xs = reinterpret_cast<uintptr_t>(sd.pts + 3 * (int64_t)t0);
-          const uintptr_t cs = reinterpret_cast<uintptr_t>(sd.covs + 6 * (int64_t)t0);
-          // head/tail cp.async and the descriptor, then the two arrivals, then bulk
-          const uintptr_t xe = xs + 12 * (uintptr_t)n, ce = cs + 24 * (uintptr_t)n;
-          const uint32_t tx = stage_range(sx, xs, xe, &S.full[s], false, stream_pol) +
-                              stage_range(sc, cs, ce, &S.full[s], false, stream_pol);
-          d.xyz_off = (int)(xs & 15);
-          d.cov_off = (int)(cs & 15);
-          S.desc[s] = d;
-          cp_async_arrive_noinc(&S.full[s]);
-          mbar_arrive_expect_tx(&S.full[s], tx);
-          stage_range(sx, xs, xe, &S.full[s], true, stream_pol);
-          stage_range(sc, cs, ce, &S.full[s], true, stream_pol);
-        }
+        S.desc[s] = d;
+        cp_async_arrive_noinc(&S.full[s]);
+        mbar_arrive_expect_tx(&S.full[s], tx);
+        stage_range(S.xyz[s], xs, xe, &S.full[s], true, stream_pol);
+        stage_range(S.cov[s], cs, ce, &S.full[s], true, stream_pol);
         ++u;
       }
     }
@@ -590,7 +542,8 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       mask = *md.vmask;
       if (L.corr_out) vbase = *md.vbase;
     }
-    const unsigned char* buf = S.buf[s];
+    const float* X = reinterpret_cast<const float*>(S.xyz[s] + d.xyz_off);
+    const float* C = reinterpret_cast<const float*>(S.cov[s] + d.cov_off);
 
     // ---- lookup: key, first probe (two 256-bit loads) of every point, resolve ----
     int idx[kPtsPerLane];
@@ -605,8 +558,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       live[k] = idx[k] < d.n;
       kx[k] = ky[k] = kz[k] = kKeyMin - 1;
       if (live[k]) {
-        float x, y, z;
-        tile_point(buf, d, idx[k], x, y, z);
+        const float x = X[3 * idx[k]], y = X[3 * idx[k] + 1], z = X[3 * idx[k] + 2];
         const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
         const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
         const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
@@ -614,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
         live[k] = key_in_range(kx[k]) && key_in_range(ky[k]) && key_in_range(kz[k]);
       }
       key[k] = live[k] ? pack_key(kx[k], ky[k], kz[k]) : kEmptyKey;
-      h[k] = lookup_home(kx[k], ky[k], kz[k]) & mask;
+      h[k] = hash_key(kx[k], ky[k], kz[k]) & mask;
       if (live[k]) {
         ld_v8(md.vslots + h[k], map_pol, sa[k]);
         ld_v8(reinterpret_cast<const char*>(md.vslots + h[k]) + 32, map_pol, sb[k]);
@@ -675,9 +627,10 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
     for (int j = lane; j < nh; j += 32) {
       const float4 e0 = H[3 * j], e1 = H[3 * j + 1], e2 = H[3 * j + 2];
       const int i = __float_as_int(e0.w);
-      float x, y, z, c[6];
-      tile_point(buf, d, i, x, y, z);
-      tile_cov(buf, d, i, c);
+      const float x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+      const float2* cv = reinterpret_cast<const float2*>(C + 6 * i);
+      const float2 c01 = cv[0], c23 = cv[1], c45 = cv[2];
+      const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
       const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
       const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
       const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
@@ -787,32 +740,6 @@ __device__ __forceinline__ void term(float* acc, const Pose32& P, float x, float
 #define VGICP_SIMPLE_MIN_BLOCKS 3
 #endif
 
-// Source point p: from the caller's rows (ps, cs: coordinate and covariance
-// rows), or (BLK) from a map's blocked grouped copy at ps (one 128-B line per
-// component for the 32 consecutive points of a warp).  The layout is a template
-// parameter so that a point loop holds the loads of one layout only.
-template <bool BLK>
-__device__ __forceinline__ void load_point(uint64_t ps, uint64_t cs, int p, float& x, float& y,
-                                           float& z, float* c) {
-  if (!BLK) {
-    const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
-    x = __ldg(pt + 0);
-    y = __ldg(pt + 1);
-    z = __ldg(pt + 2);
-    const float2* cv =
-        reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) + 6 * (int64_t)p);
-    const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
-    c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y; c[4] = c45.x; c[5] = c45.y;
-  } else {
-    const float* g = blk_point(reinterpret_cast<const float*>(ps), p);
-    x = __ldg(g);
-    y = __ldg(g + 32);
-    z = __ldg(g + 64);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c[k] = __ldg(g + 96 + 32 * k);
-  }
-}
-
 struct __align__(16) ItemConst {
   float R[9];
   float t[3];                 // R, t: 3 float4
@@ -833,101 +760,13 @@ __device__ __forceinline__ float4 lds_f4(const void* p) {
                : "r"((uint32_t)__cvta_generic_to_shared(p)));
   return v;
 }
-__device__ __forceinline__ uint64_t lds_u64(const void* p) {
-  uint64_t a;
-  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)));
-  return a;
-}
 __device__ __forceinline__ void lds_2ptr(const void* p, uint64_t& a, uint64_t& b) {
   asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
                : "=l"(a), "=l"(b)
                : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
 
-// The points [begin, end) of one work item, one per thread, accumulated into
-// acc.  Instantiated per source layout (BLK), so that the loop holds the loads of
-// one layout only (a branch on the layout inside the loop is turned into
-// predicated loads of both).
-template <int NEIGH, int MODE, bool DBG, bool BLK>
-__device__ __forceinline__ void simple_points(const LinLaunch& L, const ItemConst& ic, int begin,
-                                              int end, uint32_t vbase, uint64_t pol,
-                                              float (&acc)[kAcc]) {
-  for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
-    const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-    const float4 g3 = lds_f4(&ic.tmax);
-    uint64_t vs, ps, cs = 0;
-    lds_2ptr(&ic.vslots, vs, ps);
-    if (!BLK) cs = lds_u64(&ic.covs);  // blocked sources need no covariance pointer
-    Pose32 P;
-    P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
-    P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
-    P.R[8] = g2.x;
-    P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
-    P.tmax = g3.x;
-    MapDesc md;
-    md.vslots = reinterpret_cast<const VSlot*>(vs);
-    md.inv_r = g3.y;
-    md.margin_scale = g3.z;
-    const uint32_t mask = __float_as_uint(g3.w);
-
-    float x, y, z, c[6];
-    load_point<BLK>(ps, cs, p, x, y, z, c);
-    const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-    const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-    const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-    int kx, ky, kz;
-    {
-      // the binary64 fallback reads r from shared memory only when taken
-      const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
-      const float m = fmaf(S, md.margin_scale, 1.1920928955078125e-7f);
-      const float yx = qx * md.inv_r, yy = qy * md.inv_r, yz = qz * md.inv_r;
-      const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-      const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-      const bool ax = (rx < m) | (rx > 1.0f - m);
-      const bool ay = (ry < m) | (ry > 1.0f - m);
-      const bool az = (rz < m) | (rz > 1.0f - m);
-      kx = clamp_to_int(fx);
-      ky = clamp_to_int(fy);
-      kz = clamp_to_int(fz);
-      if (ax | ay | az) {  // rare: the descriptor and r are read only here
-        const PairDesc* pd = ic.pd;
-        MapDesc mr;
-        mr.r = ic.r;
-        if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-        if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-        if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-      }
-    }
-    if (DBG && L.qkey_out) {
-      L.qkey_out[3 * (int64_t)p + 0] = kx;
-      L.qkey_out[3 * (int64_t)p + 1] = ky;
-      L.qkey_out[3 * (int64_t)p + 2] = kz;
-    }
-    md.max_probe = ic.max_probe;
-    if (NEIGH == 1) {
-      float4 a0, a1, a2;
-      const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-      if (DBG && L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
-      if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
-      continue;
-    }
-    if (DBG && L.corr_out) {
-      float4 a0, a1, a2;
-      const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-      L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
-    }
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          float4 a0, a1, a2;
-          const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
-          if (vid < 0) continue;
-          term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
-        }
-  }
-}
-
-template <int NEIGH, int MODE, bool DBG, int LAYOUT>
+template <int NEIGH, int MODE, bool DBG>
 __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
     linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kSimpleThreads / 32][kAcc];
@@ -953,8 +792,8 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
       ic.margin_scale = md.margin_scale;
       ic.mask = *md.vmask;
       ic.vslots = md.vslots;
-      ic.pts = sd.blk ? sd.blk : sd.pts;  // blocked sources: covs == null
-      ic.covs = sd.blk ? nullptr : sd.covs;
+      ic.pts = sd.pts;
+      ic.covs = sd.covs;
       ic.pd = pd;
       ic.r = md.r;
       ic.max_probe = md.max_probe;
@@ -970,10 +809,83 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
 
-    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
-      simple_points<NEIGH, MODE, DBG, false>(L, ic, begin, end, vbase, pol, acc);
-    else
-      simple_points<NEIGH, MODE, DBG, true>(L, ic, begin, end, vbase, pol, acc);
+    for (int p = begin + threadIdx.x; p < end; p += kSimpleThreads) {
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float4 g3 = lds_f4(&ic.tmax);
+      uint64_t vs, ps, cs, pds;
+      lds_2ptr(&ic.vslots, vs, ps);
+      lds_2ptr(&ic.covs, cs, pds);
+      Pose32 P;
+      P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
+      P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
+      P.R[8] = g2.x;
+      P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
+      P.tmax = g3.x;
+      MapDesc md;
+      md.vslots = reinterpret_cast<const VSlot*>(vs);
+      md.inv_r = g3.y;
+      md.margin_scale = g3.z;
+      const uint32_t mask = __float_as_uint(g3.w);
+      const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+
+      const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
+      const float x = __ldg(pt + 0), y = __ldg(pt + 1), z = __ldg(pt + 2);
+      const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
+                                                         6 * (int64_t)p);
+      const float2 c01 = __ldg(cv + 0), c23 = __ldg(cv + 1), c45 = __ldg(cv + 2);
+      const float c[6] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y};
+      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
+      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
+      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
+      int kx, ky, kz;
+      {
+        // the binary64 fallback reads r from shared memory only when taken
+        const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
+        const float m = fmaf(S, md.margin_scale, 1.1920928955078125e-7f);
+        const float yx = qx * md.inv_r, yy = qy * md.inv_r, yz = qz * md.inv_r;
+        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+        const bool ax = (rx < m) | (rx > 1.0f - m);
+        const bool ay = (ry < m) | (ry > 1.0f - m);
+        const bool az = (rz < m) | (rz > 1.0f - m);
+        kx = clamp_to_int(fx);
+        ky = clamp_to_int(fy);
+        kz = clamp_to_int(fz);
+        if (ax | ay | az) {
+          MapDesc mr;
+          mr.r = ic.r;
+          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+        }
+      }
+      if (DBG && L.qkey_out) {
+        L.qkey_out[3 * (int64_t)p + 0] = kx;
+        L.qkey_out[3 * (int64_t)p + 1] = ky;
+        L.qkey_out[3 * (int64_t)p + 2] = kz;
+      }
+      md.max_probe = ic.max_probe;
+      if (NEIGH == 1) {
+        float4 a0, a1, a2;
+        const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+        if (DBG && L.corr_out) L.corr_out[p] = vid < 0 ? -1 : (int)((uint32_t)vid - vbase);
+        if (vid >= 0) term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+        continue;
+      }
+      if (DBG && L.corr_out) {
+        float4 a0, a1, a2;
+        const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
+        L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
+      }
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            float4 a0, a1, a2;
+            const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
+            if (vid < 0) continue;
+            term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+          }
+    }
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -1000,14 +912,10 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
 
 template <int NEIGH, int MODE>
 void launch_simple(const LinLaunch& L, int grid, cudaStream_t st) {
-  if (L.corr_out || L.qkey_out)  // single factor, the caller's rows
-    linearize_simple_kernel<NEIGH, MODE, true, kRows><<<grid, kSimpleThreads, 0, st>>>(L);
-  else if (L.src_layout == kRows)
-    linearize_simple_kernel<NEIGH, MODE, false, kRows><<<grid, kSimpleThreads, 0, st>>>(L);
-  else if (L.src_layout == kBlocked)
-    linearize_simple_kernel<NEIGH, MODE, false, kBlocked><<<grid, kSimpleThreads, 0, st>>>(L);
+  if (L.corr_out || L.qkey_out)
+    linearize_simple_kernel<NEIGH, MODE, true><<<grid, kSimpleThreads, 0, st>>>(L);
   else
-    linearize_simple_kernel<NEIGH, MODE, false, kMixed><<<grid, kSimpleThreads, 0, st>>>(L);
+    linearize_simple_kernel<NEIGH, MODE, false><<<grid, kSimpleThreads, 0, st>>>(L);
 }
 
 // ---------------------------------------------------------------------------
@@ -1032,92 +940,6 @@ __device__ __forceinline__ void eval_entry(float* acc, const float* R, const flo
   add_term_t(acc, R, e0.x, e0.y, e0.z, c, e2.y, e2.z, e2.w, e3, e4);
 }
 
-// The points of one work item (see the kernel); instantiated per source layout.
-template <bool BLK>
-__device__ __forceinline__ void compact_points(const ItemConst& ic, int begin, int end,
-                                               uint64_t pol, float (&acc)[kAcc], float4* Q,
-                                               int lane, int warp, uint32_t lt_mask) {
-  int qn = 0;  // queued entries (warp-uniform)
-  const int n = end - begin;
-
-  for (int base = warp * 32; base < n; base += kThreads) {
-    const int p = begin + base + lane;
-    bool hit = false;
-    float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-    float2 c01, c23, c45;
-    float4 a1, a2;
-    if (p < end) {
-      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-      const float4 g3 = lds_f4(&ic.tmax);
-      uint64_t vs, ps, cs, pds;
-      lds_2ptr(&ic.vslots, vs, ps);
-      lds_2ptr(&ic.covs, cs, pds);
-      {
-        float cc[6];
-        load_point<BLK>(ps, cs, p, x, y, z, cc);
-        c01 = make_float2(cc[0], cc[1]);
-        c23 = make_float2(cc[2], cc[3]);
-        c45 = make_float2(cc[4], cc[5]);
-      }
-      const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
-      const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
-      const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
-      const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
-      const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
-      const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
-      const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-      const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-      const bool ax = (rx < m) | (rx > 1.0f - m);
-      const bool ay = (ry < m) | (ry > 1.0f - m);
-      const bool az = (rz < m) | (rz > 1.0f - m);
-      int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
-      if (ax | ay | az) {
-        const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
-        MapDesc mr;
-        mr.r = ic.r;
-        if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-        if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-        if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-      }
-      MapDesc md;
-      md.vslots = reinterpret_cast<const VSlot*>(vs);
-      md.max_probe = ic.max_probe;
-      float4 a0;
-      const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
-      hit = vid >= 0;
-      tx = a0.x - qx;
-      ty = a0.y - qy;
-      tz = a0.z - qz;
-    }
-    const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
-    if (hit) {
-      float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
-      E[0] = make_float4(x, y, z, c01.x);
-      E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
-      E[2] = make_float4(c45.y, tx, ty, tz);
-      E[3] = a1;
-      E[4] = a2;
-    }
-    if (lane == 0) acc[28] += (float)__popc(hm);
-    qn += __popc(hm);
-    __syncwarp();
-    if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
-      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-      const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
-      eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
-      qn -= 32;
-      __syncwarp();
-    }
-  }
-  if (lane < qn) {  // drain the partially filled queue
-    const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-    const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
-    eval_entry(acc, R, Q + 5 * lane);
-  }
-  __syncwarp();
-}
-
-template <int LAYOUT>
 __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     linearize_compact_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
@@ -1146,8 +968,8 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
       ic.margin_scale = md.margin_scale;
       ic.mask = *md.vmask;
       ic.vslots = md.vslots;
-      ic.pts = sd.blk ? sd.blk : sd.pts;  // blocked sources: covs == null
-      ic.covs = sd.blk ? nullptr : sd.covs;
+      ic.pts = sd.pts;
+      ic.covs = sd.covs;
       ic.pd = pd;
       ic.r = md.r;
       ic.max_probe = md.max_probe;
@@ -1157,10 +979,86 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     float acc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
-    if (LAYOUT == kRows || (LAYOUT == kMixed && ic.covs != nullptr))
-      compact_points<false>(ic, begin, end, pol, acc, Q, lane, warp, lt_mask);
-    else
-      compact_points<true>(ic, begin, end, pol, acc, Q, lane, warp, lt_mask);
+    int qn = 0;  // queued entries (warp-uniform)
+    const int n = end - begin;
+
+    for (int base = warp * 32; base < n; base += kThreads) {
+      const int p = begin + base + lane;
+      bool hit = false;
+      float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+      float2 c01, c23, c45;
+      float4 a1, a2;
+      if (p < end) {
+        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+        const float4 g3 = lds_f4(&ic.tmax);
+        uint64_t vs, ps, cs, pds;
+        lds_2ptr(&ic.vslots, vs, ps);
+        lds_2ptr(&ic.covs, cs, pds);
+        const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
+        x = __ldg(pt + 0);
+        y = __ldg(pt + 1);
+        z = __ldg(pt + 2);
+        const float2* cv = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(cs) +
+                                                           6 * (int64_t)p);
+        c01 = __ldg(cv + 0);
+        c23 = __ldg(cv + 1);
+        c45 = __ldg(cv + 2);
+        const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
+        const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
+        const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
+        const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
+        const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
+        const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
+        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
+        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
+        const bool ax = (rx < m) | (rx > 1.0f - m);
+        const bool ay = (ry < m) | (ry > 1.0f - m);
+        const bool az = (rz < m) | (rz > 1.0f - m);
+        int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
+        if (ax | ay | az) {
+          const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
+          MapDesc mr;
+          mr.r = ic.r;
+          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
+          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
+          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
+        }
+        MapDesc md;
+        md.vslots = reinterpret_cast<const VSlot*>(vs);
+        md.max_probe = ic.max_probe;
+        float4 a0;
+        const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
+        hit = vid >= 0;
+        tx = a0.x - qx;
+        ty = a0.y - qy;
+        tz = a0.z - qz;
+      }
+      const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+      if (hit) {
+        float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
+        E[0] = make_float4(x, y, z, c01.x);
+        E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
+        E[2] = make_float4(c45.y, tx, ty, tz);
+        E[3] = a1;
+        E[4] = a2;
+      }
+      if (lane == 0) acc[28] += (float)__popc(hm);
+      qn += __popc(hm);
+      __syncwarp();
+      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
+        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+        const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+        eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+    if (lane < qn) {  // drain the partially filled queue
+      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+      const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+      eval_entry(acc, R, Q + 5 * lane);
+    }
+    __syncwarp();
 
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) {
@@ -1185,201 +1083,6 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
   }
 }
 }  // namespace compact
-
-// ---------------------------------------------------------------------------
-// Warp-staged per-point kernel (1 neighbour, linearization, blocked sources).
-// The per-point kernel with the stream taken off each point's dependency
-// chain: lane 0 of every warp copies the warp's next 32-point block (1,152 B,
-// contiguous in the blocked layout) into the warp's own double buffer in shared
-// memory with one bulk asynchronous copy (cp.async.bulk, completion on a
-// per-warp mbarrier) while the warp evaluates its current block.  No register
-// holds prefetched data and the copy does not pass through L1.  The waits are
-// bounded (2 s): a wait that runs out sets the status word (outputs NaN), the
-// warp stops staging and, before the kernel returns, waits (bounded) for its
-// copies in flight.
-// ---------------------------------------------------------------------------
-namespace wstage {
-constexpr int kThreads = kSimpleThreads;
-constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kBlkBytes = kBlkFloats * 4;
-
-// Orders this thread's earlier shared-memory accesses before later asynchronous
-// (bulk copy) writes to shared memory.
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ uint64_t policy_evict_normal() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-__global__ void __launch_bounds__(kThreads, VGICP_SIMPLE_MIN_BLOCKS)
-    linearize_wstage_kernel(const __grid_constant__ LinLaunch L) {
-  __shared__ float red[kWarps][kAcc];
-  __shared__ ItemConst ic;
-  __shared__ int next_item;
-  __shared__ __align__(128) float stage[kWarps][2][kBlkFloats];
-  __shared__ uint64_t bar[kWarps][2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t pol = policy_evict_last_l();
-  const uint64_t spol = policy_evict_normal();
-  if (lane == 0) {
-    mbar_init(&bar[warp][0], 1);
-    mbar_init(&bar[warp][1], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  uint32_t u = 0;         // blocks this warp has consumed (block u is in stage u & 1)
-  uint32_t issued = 0;    // blocks this warp has staged
-  bool dead = false;      // a wait ran out: stop staging
-  uint32_t dead_from = 0; // then blocks [dead_from, issued) may still be in flight
-
-  for (int it = blockIdx.x; it < L.n_items;) {
-    int pair, begin, end;
-    tma::item_bounds(L, it, pair, begin, end);
-    if (threadIdx.x == 0) {
-      const PairDesc* pd = L.pairs ? L.pairs + pair : &L.single;
-      const MapDesc md = L.maps ? L.maps[pd->map] : L.single_map;
-      const SrcDesc sd = L.srcs ? L.srcs[pd->src] : L.single_src;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) ic.R[k] = pd->R[k];
-      ic.t[0] = pd->t[0];
-      ic.t[1] = pd->t[1];
-      ic.t[2] = pd->t[2];
-      ic.tmax = pd->tmax;
-      ic.inv_r = md.inv_r;
-      ic.margin_scale = md.margin_scale;
-      ic.mask = *md.vmask;
-      ic.vslots = md.vslots;
-      ic.pts = sd.blk;  // blocked sources only
-      ic.covs = nullptr;
-      ic.pd = pd;
-      ic.r = md.r;
-      ic.max_probe = md.max_probe;
-    }
-    __syncthreads();
-
-    float acc[kAcc];
-#pragma unroll
-    for (int k = 0; k < kAcc; ++k) acc[k] = 0.0f;
-
-    const float* blk = ic.pts;
-    int p0 = begin + kBlkPts * warp;  // the warp's first block of the item
-    if (!dead && p0 < end) {
-      if (lane == 0) {
-        uint64_t* b = &bar[warp][issued & 1];
-        fence_proxy_async();
-        mbar_arrive_expect_tx(b, kBlkBytes);
-        bulk_g2s(stage[warp][issued & 1], blk + (int64_t)(p0 / kBlkPts) * kBlkFloats, kBlkBytes,
-                 b, spol);
-      }
-      ++issued;
-    }
-    for (; p0 < end; p0 += kThreads, ++u) {  // warp-uniform
-      const int s = u & 1;
-      const int pn = p0 + kThreads;
-      if (!dead && pn < end) {  // the next block into the other buffer (read last round)
-        if (lane == 0) {
-          uint64_t* b = &bar[warp][issued & 1];
-          fence_proxy_async();  // this warp's reads of that buffer before the copy's writes
-          mbar_arrive_expect_tx(b, kBlkBytes);
-          bulk_g2s(stage[warp][issued & 1], blk + (int64_t)(pn / kBlkPts) * kBlkFloats,
-                   kBlkBytes, b, spol);
-        }
-        ++issued;
-      }
-      bool ok = dead || mbar_wait(&bar[warp][s], (u >> 1) & 1);
-      ok = __all_sync(0xFFFFFFFFu, ok);
-      if (!ok && !dead) {
-        if (lane == 0) atomicExch(L.status, 1);
-        dead = true;
-        dead_from = u;
-      }
-      if (dead) continue;
-      const int p = p0 + lane;
-      float x = 0.f, y = 0.f, z = 0.f, c[6];
-      if (p < end) {
-        const float* g = stage[warp][s] + lane;
-        x = g[0];
-        y = g[32];
-        z = g[64];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) c[k] = g[96 + 32 * k];
-      }
-      __syncwarp();  // every lane has read stage s before it is refilled
-      if (p >= end) continue;
-      const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-      const float4 g3 = lds_f4(&ic.tmax);
-      Pose32 P;
-      P.R[0] = g0.x; P.R[1] = g0.y; P.R[2] = g0.z; P.R[3] = g0.w;
-      P.R[4] = g1.x; P.R[5] = g1.y; P.R[6] = g1.z; P.R[7] = g1.w;
-      P.R[8] = g2.x;
-      P.t[0] = g2.y; P.t[1] = g2.z; P.t[2] = g2.w;
-      P.tmax = g3.x;
-      const float inv_r = g3.y, margin = g3.z;
-      const uint32_t mask = __float_as_uint(g3.w);
-      const float qx = fmaf(P.R[0], x, fmaf(P.R[1], y, fmaf(P.R[2], z, P.t[0])));
-      const float qy = fmaf(P.R[3], x, fmaf(P.R[4], y, fmaf(P.R[5], z, P.t[1])));
-      const float qz = fmaf(P.R[6], x, fmaf(P.R[7], y, fmaf(P.R[8], z, P.t[2])));
-      int kx, ky, kz;
-      {
-        const float S = fabsf(x) + fabsf(y) + fabsf(z) + P.tmax;
-        const float m = fmaf(S, margin, 1.1920928955078125e-7f);
-        const float yx = qx * inv_r, yy = qy * inv_r, yz = qz * inv_r;
-        const float fx = floorf(yx), fy = floorf(yy), fz = floorf(yz);
-        const float rx = yx - fx, ry = yy - fy, rz = yz - fz;
-        const bool ax = (rx < m) | (rx > 1.0f - m);
-        const bool ay = (ry < m) | (ry > 1.0f - m);
-        const bool az = (rz < m) | (rz > 1.0f - m);
-        kx = clamp_to_int(fx);
-        ky = clamp_to_int(fy);
-        kz = clamp_to_int(fz);
-        if (ax | ay | az) {  // rare: the descriptor and r are read only here
-          const PairDesc* pd = ic.pd;
-          MapDesc mr;
-          mr.r = ic.r;
-          if (ax) kx = axis_key_f64(pd, mr, 0, x, y, z);
-          if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
-          if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
-        }
-      }
-      MapDesc md;
-      md.vslots = ic.vslots;
-      md.max_probe = ic.max_probe;
-      float4 a0, a1, a2;
-      const int vid = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
-      if (vid >= 0) add_term(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
-    }
-
-#pragma unroll
-    for (int k = 0; k < kAcc; ++k) {
-      float v = acc[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-      acc[k] = v;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < kAcc; ++k) red[warp][k] = acc[k];
-    }
-    if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(L.status + 1, 1);
-    __syncthreads();
-    if (threadIdx.x < kAcc) {
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += (double)red[w][threadIdx.x];
-      L.partials[(int64_t)it * kPartialStride + threadIdx.x] = s;
-    }
-    it = next_item;  // read between the two barriers; rewritten only after the second
-    __syncthreads();
-  }
-  if (dead && lane == 0) {
-    // let this warp's copies in flight land before the block exits
-    for (uint32_t v = dead_from; v < issued; ++v) mbar_wait(&bar[warp][v & 1], (v >> 1) & 1);
-  }
-}
-}  // namespace wstage
-
 
 
 // One warp per pair: lane k sums term k over the pair's items in order.  For the
@@ -1480,8 +1183,7 @@ int default_variant() { return 1; }
 
 int linearize_grid(int neighbours, int variant) {
   if (variant == 0) variant = default_variant();
-  if (neighbours == 27 || variant == 1 || variant == 4)
-    return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
+  if (neighbours == 27 || variant == 1) return device_sm_count() * VGICP_SIMPLE_MIN_BLOCKS;
   if (variant == 3) return device_sm_count() * VGICP_COMPACT_MIN_BLOCKS;
   return device_sm_count() * VGICP_MIN_BLOCKS;
 }
@@ -1508,17 +1210,8 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
-  } else if (variant == 4 && L.src_layout == kBlocked && L.neighbours == 1) {
-    wstage::linearize_wstage_kernel<<<grid, wstage::kThreads, 0, st>>>(L);
-  } else if (variant == 4) {
-    launch_simple<1, 0>(L, grid, st);  // the warp-staged kernel reads blocked sources only
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
-    if (L.src_layout == kRows)
-      compact::linearize_compact_kernel<kRows><<<grid, compact::kThreads, 0, st>>>(L);
-    else if (L.src_layout == kBlocked)
-      compact::linearize_compact_kernel<kBlocked><<<grid, compact::kThreads, 0, st>>>(L);
-    else
-      compact::linearize_compact_kernel<kMixed><<<grid, compact::kThreads, 0, st>>>(L);
+    compact::linearize_compact_kernel<<<grid, compact::kThreads, 0, st>>>(L);
   } else if (variant == 3) {
     launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
 

@@ -59,7 +59,6 @@ namespace {
 constexpr int kMinItem = 2048;
 
 int build_items(vgicp_plan* P, int item) {
-  item = (item + kBlkPts - 1) / kBlkPts * kBlkPts;  // items start on 32-point blocks
   std::vector<WorkItem> items;
   std::vector<int2> span((size_t)P->n_pairs);
   for (int64_t q = 0; q < P->n_pairs; ++q) {
@@ -91,7 +90,6 @@ LinLaunch launch_of(const vgicp_plan* P) {
   L.pairs = P->d_pd;
   L.maps = P->d_md;
   L.srcs = P->d_sd;
-  L.src_layout = sources_layout(P->sd.data(), P->sd.size());
   L.partials = P->d_partials;
   L.status = P->d_status;
   L.neighbours = P->neighbours;
@@ -240,8 +238,8 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
   const int neighbours = opts && opts->neighbours ? opts->neighbours : 1;
   if (neighbours != 1 && neighbours != 27)
     return set_error(VGICP_ERR_INVALID_ARG, "neighbours must be 1 or 27");
-  if (opts && (opts->variant < 0 || opts->variant > 4))
-    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0 to 4");
+  if (opts && (opts->variant < 0 || opts->variant > 3))
+    return set_error(VGICP_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   if (opts && (opts->corr_out || opts->qkey_out))
     return set_error(VGICP_ERR_INVALID_ARG, "corr_out/qkey_out are single-factor options");
   if (opts && opts->tile > 0 && opts->tile < kMinItem)
@@ -264,15 +262,14 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
     if (sources[c].map) {
       const vgicp_map* m = sources[c].map;
       const int64_t a = m->set->point_off[m->index], b = m->set->point_off[m->index + 1];
-      P->sd.push_back(SrcDesc{nullptr, nullptr, b - a,
-                              m->set->d_gblk + kBlkFloats * m->set->gblk_off[(size_t)m->index]});
+      P->sd.push_back(SrcDesc{m->set->d_gpts + 3 * a, m->set->d_gcovs + 6 * a, b - a});
     } else {
       int rc = check_cloud(sources[c].points, sources[c].covs, sources[c].n, "source cloud");
       if (rc) {
         destroy_plan(P);
         return rc;
       }
-      P->sd.push_back(SrcDesc{sources[c].points, sources[c].covs, sources[c].n, nullptr});
+      P->sd.push_back(SrcDesc{sources[c].points, sources[c].covs, sources[c].n});
     }
     P->src_n.push_back(P->sd.back().n);
   }
@@ -365,7 +362,7 @@ int vgicp_plan_autotune(vgicp_plan* P, const double* poses, vgicp_stream_t strea
   rc = upload_poses(P, buf, st);
   if (rc) return rc;
   VGICP_CUDA_TRY(cudaStreamSynchronize(st));
-  const int variants_1[] = {1, 2, 3, 4};
+  const int variants_1[] = {1, 2, 3};
   const int variants_27[] = {1};
   const int* vs = P->neighbours == 27 ? variants_27 : variants_1;
   const int nv = P->neighbours == 27 ? 1 : (int)(sizeof(variants_1) / sizeof(variants_1[0]));

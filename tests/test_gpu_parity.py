@@ -281,7 +281,7 @@ def test_pose_validation(dev):
 
 
 @pytest.mark.parametrize("pose", ["planted", "perturbed"])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_kernel_variants_match_oracle(dev, variant, pose):
     tp, tc, sp, sc, T, r = cases.room()
     if pose == "perturbed":
@@ -297,7 +297,7 @@ def test_kernel_variants_match_oracle(dev, variant, pose):
     check_factor(bat.out[0], bat.inliers[0], ref, f"batched variant {variant}", planted=planted)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_map_as_source(dev, variant):
     """A map's own (voxel-grouped) cloud as the source gives the same factor as the
     original cloud, within tolerance, and matches the oracle."""
@@ -331,7 +331,7 @@ def test_plan_graph_autotune_matches_oracle_and_batched(dev):
     maps[0].status()
     plan = api.Plan(maps, maps, w.pairs)
     info = plan.autotune(w.poses)
-    assert info["variant"] in (1, 2, 3, 4) and info["item_points"] in (4096, 8192, 16384, 32768)
+    assert info["variant"] in (1, 2, 3) and info["item_points"] in (4096, 8192, 16384, 32768)
     a = plan.execute(w.poses).out.clone()
     b = plan.execute(w.poses).out.clone()
     assert torch.equal(a, b)
