@@ -593,7 +593,9 @@ def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution
                        neighbours=27, tile=0, stream=None, kernel_events=None):
     """Linearize factors among submaps that live in host memory, batch by batch:
     each batch's submaps are uploaded, built into voxel maps (which also serve
-    as the sources), linearized in one batched launch, and released.
+    as the sources) and linearized in one batched launch.  Consecutive batches
+    whose submaps have the same sizes reuse one set of device buffers and maps
+    (rebuilt in place); the last set is released at the end.
     ``points_host`` / ``covs_host``: numpy arrays or CPU tensors (pinned tensors
     upload at full speed).  Returns (out (P, 43) float64 host, inliers (P,) host,
     n_batches).  ``kernel_events``: optional list; each batch appends the
@@ -607,32 +609,51 @@ def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution
     out = np.zeros((P, RESULT_SIZE))
     inl = np.zeros(P, dtype=np.int64)
     dev = torch.device("cuda", torch.cuda.current_device())
-    for b in range(nb):
-        sel = np.nonzero(batch == b)[0]
-        used = np.unique(pairs[sel].ravel())
-        local = {int(m): k for k, m in enumerate(used)}
-        boff = np.concatenate([[0], np.cumsum(sizes[used])]).astype(np.int64)
-        pts = torch.empty((int(boff[-1]), 3), dtype=torch.float32, device=dev)
-        cvs = torch.empty((int(boff[-1]), 6), dtype=torch.float32, device=dev)
-        for k, m in enumerate(used):
-            pts[boff[k]:boff[k + 1]].copy_(_host_rows(points_host, off[m], off[m + 1]),
-                                           non_blocking=True)
-            cvs[boff[k]:boff[k + 1]].copy_(_host_rows(covs_host, off[m], off[m + 1]),
-                                           non_blocking=True)
-        maps = build_voxelmaps(pts, cvs, boff, resolution, stream=stream)
-        maps[0].status()
-        lp = np.array([[local[int(j)], local[int(i)]] for j, i in pairs[sel]], dtype=np.int32)
-        ev = None
-        if kernel_events is not None:
-            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for e in ev:  # creates the CUDA event the library then records
-                e.record()
-            kernel_events.append(ev)
-        res = linearize_batched(maps, maps, lp, poses[sel], neighbours=neighbours, tile=tile,
-                                events=ev, stream=stream)
-        out[sel] = res.out.cpu().numpy()
-        inl[sel] = res.inliers.cpu().numpy()
-        for m in maps:
-            m.close()
-        del pts, cvs
+    # the device buffers and voxel maps of the last batch: a batch whose submaps
+    # have the same sizes, in order, refills them (a rebuild allocates nothing)
+    # instead of allocating and freeing its own; one batch is resident at a time
+    held = None  # (sizes, pts, cvs, maps)
+    try:
+        for b in range(nb):
+            sel = np.nonzero(batch == b)[0]
+            used = np.unique(pairs[sel].ravel())
+            local = {int(m): k for k, m in enumerate(used)}
+            bsizes = tuple(int(x) for x in sizes[used])
+            boff = np.concatenate([[0], np.cumsum(sizes[used])]).astype(np.int64)
+            reuse = held is not None and held[0] == bsizes
+            if not reuse:
+                if held is not None:
+                    for m in held[3]:
+                        m.close()
+                    held = None
+                pts = torch.empty((int(boff[-1]), 3), dtype=torch.float32, device=dev)
+                cvs = torch.empty((int(boff[-1]), 6), dtype=torch.float32, device=dev)
+            else:
+                _, pts, cvs, maps = held
+            for k, m in enumerate(used):
+                pts[boff[k]:boff[k + 1]].copy_(_host_rows(points_host, off[m], off[m + 1]),
+                                               non_blocking=True)
+                cvs[boff[k]:boff[k + 1]].copy_(_host_rows(covs_host, off[m], off[m + 1]),
+                                               non_blocking=True)
+            if reuse:
+                rebuild_voxelmaps(maps, pts, cvs, stream=stream)
+            else:
+                maps = build_voxelmaps(pts, cvs, boff, resolution, stream=stream)
+                held = (bsizes, pts, cvs, maps)
+            lp = np.array([[local[int(j)], local[int(i)]] for j, i in pairs[sel]], dtype=np.int32)
+            ev = None
+            if kernel_events is not None:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for e in ev:  # creates the CUDA event the library then records
+                    e.record()
+                kernel_events.append(ev)
+            res = linearize_batched(maps, maps, lp, poses[sel], neighbours=neighbours, tile=tile,
+                                    events=ev, stream=stream)
+            out[sel] = res.out.cpu().numpy()
+            inl[sel] = res.inliers.cpu().numpy()
+            maps[0].status()  # a device-side build error of this batch raises here
+    finally:
+        if held is not None:
+            for m in held[3]:
+                m.close()
     return out, inl, nb
