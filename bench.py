@@ -64,7 +64,8 @@ def parse_args(argv=None):
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0,
-                    help="1-neighbour kernel: 0 auto, 1 per-point, 2 shared-memory staged")
+                    help="kernel: 0 auto, 1 per-point, 2 shared-memory staged (1 neighbour), "
+                         "3 hit-compacting (1 or 27 neighbours)")
     ap.add_argument("--sources", choices=["maps", "clouds"], default="maps",
                     help="maps: each submap's own (voxel-grouped) cloud is the source of its "
                          "factors; clouds: the caller's arrays as given")
@@ -526,6 +527,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # the pinned host-to-device bandwidth on its own (one upload, copy stream idle
+    # otherwise): the end-to-end step hides the upload only while it is shorter
+    # than the device step
+    e0.record(cstream)
+    with torch.cuda.stream(cstream):
+        bufs[1][0].copy_(pts_h, non_blocking=True)
+        bufs[1][1].copy_(covs_h, non_blocking=True)
+    e1.record(cstream)
+    torch.cuda.synchronize()
+    h2d_alone_ms = e0.elapsed_time(e1)
     barrier(world)
     e0.record(stream)
     e2e_run(E, start_event=e0)
@@ -585,6 +596,7 @@ def run_ours(args):
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"},
             "e2e": {"value": e2e_value, "unit": "source pts/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "h2d_alone": {"ms": h2d_alone_ms, "GB/s": h2d / (h2d_alone_ms / 1e3) / 1e9},
                     "pipelining": "upload of step k+1 (copy stream, second buffer) overlaps "
                                   "step k"},
             "batched_vs_per_factor": comparison,
@@ -750,7 +762,8 @@ def run_workload(args):
             state["ev"] = []
             state["r"] = api.linearize_admitted(pts_h, covs_h, w.clouds.offsets,
                                                 w.pairs, w.poses, w.resolution, budget=budget,
-                                                neighbours=27, kernel_events=state["ev"])
+                                                neighbours=27, kernel_events=state["ev"],
+                                                variant=args.variant, tile=args.tile)
         n_pts = int(w.source_points_per_step)
         name = (f"large_map_{len(w.clouds.offsets) - 1}submaps_x100k_{w.pairs.shape[0]}pairs"
                 f"_r0.5_27neighbours")

@@ -590,7 +590,7 @@ def _host_rows(x, a, b):
 
 
 def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution, budget,
-                       neighbours=27, tile=0, stream=None, kernel_events=None):
+                       neighbours=27, tile=0, stream=None, kernel_events=None, variant=0):
     """Linearize factors among submaps that live in host memory, batch by batch:
     each batch's submaps are uploaded, built into voxel maps (which also serve
     as the sources) and linearized in one batched launch.  Consecutive batches
@@ -648,7 +648,7 @@ def linearize_admitted(points_host, covs_host, offsets, pairs, poses, resolution
                     e.record()
                 kernel_events.append(ev)
             res = linearize_batched(maps, maps, lp, poses[sel], neighbours=neighbours, tile=tile,
-                                    events=ev, stream=stream)
+                                    variant=variant, events=ev, stream=stream)
             out[sel] = res.out.cpu().numpy()
             inl[sel] = res.inliers.cpu().numpy()
             maps[0].status()  # a device-side build error of this batch raises here
