@@ -64,8 +64,8 @@ def parse_args(argv=None):
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0,
-                    help="kernel: 0 auto, 1 per-point, 2 shared-memory staged (1 neighbour), "
-                         "3 hit-compacting (1 or 27 neighbours)")
+                    help="1-neighbour kernel: 0 auto, 1 per-point, 2 shared-memory staged, "
+                         "3 hit-compacting (27 neighbours always use 1)")
     ap.add_argument("--sources", choices=["maps", "clouds"], default="maps",
                     help="maps: each submap's own (voxel-grouped) cloud is the source of its "
                          "factors; clouds: the caller's arrays as given")

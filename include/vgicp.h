@@ -159,13 +159,11 @@ typedef struct {
                          one independent term each; 0 = 1 */
   int32_t tile;       /* source points per work item; 0 = automatic */
   int32_t grid;       /* CTAs of the persistent launch; 0 = automatic */
-  int32_t variant;    /* kernel: 0 = automatic, 1 = one point per thread,
-                         2 = shared-memory staged (bulk asynchronous copies;
-                             1 neighbour only, 27 uses kernel 1),
+  int32_t variant;    /* 1-neighbour kernel: 0 = automatic, 1 = one point per thread,
+                         2 = shared-memory staged (bulk asynchronous copies),
                          3 = per-warp hit compaction (terms evaluated in full
-                             warps from a shared-memory queue; 1 or 27
-                             neighbours); the debug outputs corr_out / qkey_out
-                             always use kernel 1 */
+                             warps from a shared-memory queue); the debug outputs
+                             corr_out / qkey_out always use kernel 1 */
   int32_t* corr_out;  /* optional device, n_src (single factor only): index of the
                          point's own voxel (first-appearance numbering) or -1 */
   int32_t* qkey_out;  /* optional device, n_src x 3 (single factor only): key of T mu */
@@ -357,7 +355,7 @@ int vgicp_plan_create(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud*
                       int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                       const vgicp_lin_opts* opts, vgicp_stream_t stream, vgicp_plan** out);
 
-/* Synchronizes.  Times each kernel variant (1 neighbour: 1, 2, 3; 27: 1, 3) with work items
+/* Synchronizes.  Times each kernel variant (1-neighbour: 1, 2, 3) with work items
  * of 4096, 8192, 16384 and 32768 points on these poses (host, n_pairs x 16) and
  * keeps the fastest; results then depend (within float32 rounding) on that
  * choice, and are deterministic for it. */

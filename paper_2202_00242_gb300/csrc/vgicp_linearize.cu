@@ -940,7 +940,6 @@ __device__ __forceinline__ void eval_entry(float* acc, const float* R, const flo
   add_term_t(acc, R, e0.x, e0.y, e0.z, c, e2.y, e2.z, e2.w, e3, e4);
 }
 
-template <int NEIGH>
 __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     linearize_compact_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ __align__(16) float4 queue[kWarps][kQueue * 5];
@@ -983,21 +982,18 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
     int qn = 0;  // queued entries (warp-uniform)
     const int n = end - begin;
 
-    for (int base = warp * 32; base < n; base += kThreads) {  // warp-uniform
+    for (int base = warp * 32; base < n; base += kThreads) {
       const int p = begin + base + lane;
-      const bool live = p < end;
-      float x = 0.f, y = 0.f, z = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
-      float2 c01 = make_float2(0.f, 0.f), c23 = c01, c45 = c01;
-      int kx = 0, ky = 0, kz = 0;
-      uint64_t vs = 0;
-      uint32_t mask = 0;
-      if (live) {
+      bool hit = false;
+      float x = 0.f, y = 0.f, z = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+      float2 c01, c23, c45;
+      float4 a1, a2;
+      if (p < end) {
         const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
         const float4 g3 = lds_f4(&ic.tmax);
-        uint64_t ps, cs, pds;
+        uint64_t vs, ps, cs, pds;
         lds_2ptr(&ic.vslots, vs, ps);
         lds_2ptr(&ic.covs, cs, pds);
-        mask = __float_as_uint(g3.w);
         const float* pt = reinterpret_cast<const float*>(ps) + 3 * (int64_t)p;
         x = __ldg(pt + 0);
         y = __ldg(pt + 1);
@@ -1007,9 +1003,9 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
         c01 = __ldg(cv + 0);
         c23 = __ldg(cv + 1);
         c45 = __ldg(cv + 2);
-        qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
-        qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
-        qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
+        const float qx = fmaf(g0.x, x, fmaf(g0.y, y, fmaf(g0.z, z, g2.y)));
+        const float qy = fmaf(g0.w, x, fmaf(g1.x, y, fmaf(g1.y, z, g2.z)));
+        const float qz = fmaf(g1.z, x, fmaf(g1.w, y, fmaf(g2.x, z, g2.w)));
         const float S = fabsf(x) + fabsf(y) + fabsf(z) + g3.x;
         const float m = fmaf(S, g3.z, 1.1920928955078125e-7f);
         const float yx = qx * g3.y, yy = qy * g3.y, yz = qz * g3.y;
@@ -1018,9 +1014,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
         const bool ax = (rx < m) | (rx > 1.0f - m);
         const bool ay = (ry < m) | (ry > 1.0f - m);
         const bool az = (rz < m) | (rz > 1.0f - m);
-        kx = clamp_to_int(fx);
-        ky = clamp_to_int(fy);
-        kz = clamp_to_int(fz);
+        int kx = clamp_to_int(fx), ky = clamp_to_int(fy), kz = clamp_to_int(fz);
         if (ax | ay | az) {
           const PairDesc* pd = reinterpret_cast<const PairDesc*>(pds);
           MapDesc mr;
@@ -1029,41 +1023,34 @@ __global__ void __launch_bounds__(kThreads, VGICP_COMPACT_MIN_BLOCKS)
           if (ay) ky = axis_key_f64(pd, mr, 1, x, y, z);
           if (az) kz = axis_key_f64(pd, mr, 2, x, y, z);
         }
+        MapDesc md;
+        md.vslots = reinterpret_cast<const VSlot*>(vs);
+        md.max_probe = ic.max_probe;
+        float4 a0;
+        const int vid = lookup(md, __float_as_uint(g3.w), kx, ky, kz, pol, a0, a1, a2);
+        hit = vid >= 0;
+        tx = a0.x - qx;
+        ty = a0.y - qy;
+        tz = a0.z - qz;
       }
-      // the point's voxel (NEIGH = 1) or the 27 voxels of its 3x3x3 block, in
-      // dz, dy, dx order: every hit is queued, and every full warp of queued
-      // terms evaluated with all lanes busy
-      for (int o = 0; o < NEIGH; ++o) {  // the same trip count on every lane
-        const int dx = NEIGH == 1 ? 0 : o % 3 - 1;
-        const int dy = NEIGH == 1 ? 0 : (o / 3) % 3 - 1;
-        const int dz = NEIGH == 1 ? 0 : o / 9 - 1;
-        bool hit = false;
-        float4 a0, a1, a2;
-        if (live) {
-          MapDesc md;
-          md.vslots = reinterpret_cast<const VSlot*>(vs);
-          md.max_probe = ic.max_probe;
-          hit = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2) >= 0;
-        }
-        const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
-        if (hit) {
-          float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
-          E[0] = make_float4(x, y, z, c01.x);
-          E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
-          E[2] = make_float4(c45.y, a0.x - qx, a0.y - qy, a0.z - qz);
-          E[3] = a1;
-          E[4] = a2;
-        }
-        if (lane == 0) acc[28] += (float)__popc(hm);
-        qn += __popc(hm);
+      const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hit);
+      if (hit) {
+        float4* E = Q + 5 * (qn + __popc(hm & lt_mask));
+        E[0] = make_float4(x, y, z, c01.x);
+        E[1] = make_float4(c01.y, c23.x, c23.y, c45.x);
+        E[2] = make_float4(c45.y, tx, ty, tz);
+        E[3] = a1;
+        E[4] = a2;
+      }
+      if (lane == 0) acc[28] += (float)__popc(hm);
+      qn += __popc(hm);
+      __syncwarp();
+      if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
+        const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
+        const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
+        eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
+        qn -= 32;
         __syncwarp();
-        if (qn >= 32) {  // one full warp of terms: lane l takes entry qn - 32 + l
-          const float4 g0 = lds_f4(&ic.R[0]), g1 = lds_f4(&ic.R[4]), g2 = lds_f4(&ic.R[8]);
-          const float R[9] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
-          eval_entry(acc, R, Q + 5 * (qn - 32 + lane));
-          qn -= 32;
-          __syncwarp();
-        }
       }
     }
     if (lane < qn) {  // drain the partially filled queue
@@ -1219,14 +1206,12 @@ int launch_linearize(const LinLaunch& L, cudaStream_t st) {
       else if (L.mode == 3) launch_simple<1, 3>(L, grid, st);
       else launch_simple<1, 4>(L, grid, st);
     }
-  } else if (L.neighbours == 27 && variant == 3 && !L.corr_out && !L.qkey_out) {
-    compact::linearize_compact_kernel<27><<<grid, compact::kThreads, 0, st>>>(L);
   } else if (L.neighbours == 27) {
     launch_simple<27, 0>(L, grid, st);
   } else if (variant == 1) {
     launch_simple<1, 0>(L, grid, st);
   } else if (variant == 3 && !L.corr_out && !L.qkey_out) {
-    compact::linearize_compact_kernel<1><<<grid, compact::kThreads, 0, st>>>(L);
+    compact::linearize_compact_kernel<<<grid, compact::kThreads, 0, st>>>(L);
   } else if (variant == 3) {
     launch_simple<1, 0>(L, grid, st);  // the per-point kernel writes the debug outputs
 

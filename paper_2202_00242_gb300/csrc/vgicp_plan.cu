@@ -363,10 +363,9 @@ int vgicp_plan_autotune(vgicp_plan* P, const double* poses, vgicp_stream_t strea
   if (rc) return rc;
   VGICP_CUDA_TRY(cudaStreamSynchronize(st));
   const int variants_1[] = {1, 2, 3};
-  const int variants_27[] = {1, 3};
+  const int variants_27[] = {1};
   const int* vs = P->neighbours == 27 ? variants_27 : variants_1;
-  const int nv = P->neighbours == 27 ? (int)(sizeof(variants_27) / sizeof(variants_27[0]))
-                                     : (int)(sizeof(variants_1) / sizeof(variants_1[0]));
+  const int nv = P->neighbours == 27 ? 1 : (int)(sizeof(variants_1) / sizeof(variants_1[0]));
   const int items[] = {4096, 8192, 16384, 32768};
   float best = 1e30f;
   int best_v = 1, best_i = default_item_size();

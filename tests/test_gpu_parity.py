@@ -182,7 +182,7 @@ def test_outdoor_submaps_batched(dev):
 
 
 @pytest.mark.parametrize("pose", ["planted", "perturbed"])
-@pytest.mark.parametrize("mode", ["single", "batched", "batched_compacting"])
+@pytest.mark.parametrize("mode", ["single", "batched"])
 def test_27_neighbours_match_oracle(dev, mode, pose):
     tp, tc, sp, sc, T, r = cases.room(seed=4, n_target=4096, n_source=3000)
     if pose == "perturbed":
@@ -196,7 +196,7 @@ def test_27_neighbours_match_oracle(dev, mode, pose):
         out, inl = lin.out, lin.inliers
     else:
         bat = api.linearize_batched([vm], [(cu(sp), cu(sc))], [[0, 0]], T[None], neighbours=27,
-                                    tile=512, variant=3 if mode == "batched_compacting" else 0)
+                                    tile=512)
         out, inl = bat.out[0], bat.inliers[0]
     check_factor(out, inl, ref, mode, planted=pose == "planted")
 
