@@ -243,6 +243,18 @@ int vgicp_evaluate_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_c
                            const double* poses, int32_t mode, double* out, int64_t* inliers,
                            const vgicp_lin_opts* opts, vgicp_stream_t stream);
 
+/* The backward pass of the differentiable factor (Sec. III-A: the gradient of
+ * Eq. 2 with respect to the pose increment): the gradient of each factor's err,
+ * 2 J^T W d with W held (exact = 0, the Gauss-Newton gradient, twice the b of
+ * vgicp_linearize), or the exact gradient (exact = 1).  vgicp_evaluate_batched
+ * with mode 2 or 3; same arguments, out: device n_pairs x 7 (gradient 6, err 1).
+ * For poses composed on the device and the incoming gradient applied there, see
+ * vgicp_plan_evaluate. */
+int vgicp_backward_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                           int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                           const double* poses, int32_t exact, double* out, int64_t* inliers,
+                           const vgicp_lin_opts* opts, vgicp_stream_t stream);
+
 /* Host binary64 pose algebra for optimizers (no device work; never fails on
  * finite input except solve6 on a non positive definite system).
  *   vgicp_se3_exp: T (row-major 4x4) = Exp(xi), xi = [omega; v].

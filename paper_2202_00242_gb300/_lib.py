@@ -52,6 +52,8 @@ SIGNATURES = {
                                                P, i64, P, P, P, ctypes.POINTER(LinOpts), P]),
     "vgicp_evaluate_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
                                               P, i64, P, i32, P, P, ctypes.POINTER(LinOpts), P]),
+    "vgicp_backward_batched": (ctypes.c_int, [ctypes.POINTER(P), i32, ctypes.POINTER(Cloud), i32,
+                                              P, i64, P, i32, P, P, ctypes.POINTER(LinOpts), P]),
     "vgicp_se3_exp": (ctypes.c_int, [P, P]),
     "vgicp_se3_right_jacobian": (ctypes.c_int, [P, P]),
     "vgicp_pose_mul": (ctypes.c_int, [P, P, P]),

@@ -446,6 +446,29 @@ def evaluate_batched(maps, sources, pairs, poses, mode=GRADIENT, neighbours=1, t
     return out[:, :6], out[:, 6], inl
 
 
+def backward_batched(maps, sources, pairs, poses, exact=False, neighbours=1, tile=0,
+                     stream=None):
+    """Gradient of each factor's err with respect to its pose increment: 2 J^T W d
+    with W held (``exact=False``) or the exact gradient.  Returns (grad (P, 6),
+    err (P,), inliers (P,)), device."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0]
+    poses = _pose_array(poses, P)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((P, 7), dtype=torch.float64, device=dev)
+    inl = torch.empty(P, dtype=torch.int64, device=dev)
+    clouds = make_clouds(sources)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    opts = LinOpts(int(neighbours), int(tile), 0, 0, None, None, None, None)
+    check(_lib.load().vgicp_backward_batched(arr, len(maps), clouds, len(sources),
+                                             pairs.ctypes.data_as(ctypes.c_void_p), P,
+                                             poses.ctypes.data_as(ctypes.c_void_p),
+                                             1 if exact else 0, ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(inl.data_ptr()), ctypes.byref(opts),
+                                             _stream_ptr(stream)))
+    return out[:, :6], out[:, 6], inl
+
+
 def downsample(points: torch.Tensor, resolution: float, times: torch.Tensor | None = None,
                split: float = 0.0, offsets=None, stream=None):
     """Voxel-grid downsampling with timestamp averaging (Sec. III-C).  Returns

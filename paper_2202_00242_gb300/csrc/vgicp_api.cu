@@ -488,6 +488,15 @@ int vgicp_evaluate_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_c
                       stream, mode);
 }
 
+int vgicp_backward_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
+                           int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
+                           const double* poses, int32_t exact, double* out, int64_t* inliers,
+                           const vgicp_lin_opts* opts, vgicp_stream_t stream) {
+  if (exact != 0 && exact != 1) return set_error(VGICP_ERR_INVALID_ARG, "exact must be 0 or 1");
+  return batched_impl(maps, n_maps, sources, n_sources, pairs, n_pairs, poses, out, inliers, opts,
+                      stream, exact ? 3 : 2);
+}
+
 int vgicp_overlap_batched(vgicp_map* const* maps, int32_t n_maps, const vgicp_cloud* sources,
                           int32_t n_sources, const int32_t* pairs, int64_t n_pairs,
                           const double* poses, int64_t* inliers, const vgicp_lin_opts* opts,

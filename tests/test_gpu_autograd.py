@@ -78,6 +78,32 @@ def test_evaluate_modes_match_oracle(small_set):
             assert abs(float(e[p]) - ref.err) <= 1e-4 * ref.err
 
 
+def test_backward_batched_is_the_gradient_mode(small_set):
+    """vgicp_backward_batched gives the gradient modes of vgicp_evaluate_batched,
+    bit for bit, and rejects an exact flag other than 0 or 1."""
+    import ctypes
+    from paper_2202_00242_gb300 import _lib
+    w, maps, srcs, omaps = small_set
+    for exact, mode in ((False, api.GRADIENT), (True, api.EXACT_GRADIENT)):
+        g, e, i = api.backward_batched(maps, srcs, w.pairs, w.poses, exact=exact)
+        g2, e2, i2 = api.evaluate_batched(maps, srcs, w.pairs, w.poses, mode=mode)
+        assert torch.equal(g, g2) and torch.equal(e, e2) and torch.equal(i, i2)
+    lib = _lib.load()
+    clouds = api.make_clouds(srcs)
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    pairs = np.ascontiguousarray(w.pairs, dtype=np.int32)
+    poses = np.ascontiguousarray(w.poses, dtype=np.float64)
+    out = torch.empty((len(pairs), 7), dtype=torch.float64, device="cuda")
+    inl = torch.empty(len(pairs), dtype=torch.int64, device="cuda")
+    rc = lib.vgicp_backward_batched(arr, len(maps), clouds, len(srcs),
+                                    pairs.ctypes.data_as(ctypes.c_void_p), len(pairs),
+                                    poses.ctypes.data_as(ctypes.c_void_p), 2,
+                                    ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(inl.data_ptr()), None,
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1
+
+
 def test_autograd_backward_vs_finite_differences(small_set):
     """d err / d xi at a nonzero xi: the backward kernel (exact mode) composed with
     the SE(3) right Jacobian vs binary64 central differences of the oracle's cost
