@@ -183,18 +183,13 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
 // slot, claiming a slot with a CAS on the key; a key placed past its home sets
 // the home slot's spill flag.  lslot_of[v] records the slot (kNoSlot if the
 // probe limit was reached, which is reported as VGICP_ERR_HASH_FULL).
+// lo: the voxel's map.
 __device__ __forceinline__ void insert_lookup(uint32_t v, unsigned long long key, uint32_t c,
-                                              const float* q, int32_t n_maps,
-                                              const uint32_t* __restrict__ vbase,
+                                              const float* q, int lo,
                                               const int64_t* __restrict__ slot_base,
                                               const uint32_t* __restrict__ vmask,
                                               int32_t max_probe, VSlot* vslots,
                                               uint32_t* __restrict__ lslot_of, int32_t* status) {
-  int lo = 0, hi = n_maps;  // last m with vbase[m] <= v
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (vbase[mid] <= v) lo = mid; else hi = mid;
-  }
   const unsigned long long fm = (1ull << kKeyBits) - 1ull;
   const int kx = (int)((key >> (2 * kKeyBits)) & fm) - kKeyBias;
   const int ky = (int)((key >> kKeyBits) & fm) - kKeyBias;
@@ -268,6 +263,17 @@ __device__ __forceinline__ void insertion_sort(uint32_t* L, uint32_t c) {
   }
 }
 
+// Map of rank (or voxel id) r: the last m with vbase[m] <= r.
+__device__ __forceinline__ int map_of_rank(const uint32_t* __restrict__ vbase, int32_t n_maps,
+                                           int64_t r) {
+  int lo = 0, hi = n_maps;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)vbase[mid] <= r) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     int64_t n_max, const uint32_t* __restrict__ n_vox, const uint32_t* __restrict__ n_valid,
     const float* __restrict__ pts, const float* __restrict__ covs,
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     const uint32_t* __restrict__ vmask, int32_t max_probe, VSlot* vslots,
     uint32_t* __restrict__ lslot_of, int32_t* status) {
   __shared__ uint32_t stage[kFinStage];
+  __shared__ int seg_map[2];
   const int64_t V = min((int64_t)*n_vox, n_max);
   const uint32_t total = *n_valid;  // end of the last list (goff[V] is not stored)
   for (int64_t r0 = (int64_t)blockIdx.x * kFinThreads; r0 < V; r0 += (int64_t)gridDim.x * kFinThreads) {
@@ -289,6 +296,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
     const bool staged = len <= (uint32_t)kFinStage;
     const int64_t r = r0 + threadIdx.x;
     const bool mine = r < r1;
+    if (threadIdx.x == 0) {  // the maps of the CTA's first and last ranks
+      seg_map[0] = map_of_rank(vbase, n_maps, r0);
+      seg_map[1] = map_of_rank(vbase, n_maps, r1 - 1);
+    }
     const uint32_t v = mine ? vorder[r] : 0u;
     const uint32_t o = mine ? goff[r] : 0u;
     const uint32_t c = mine ? (r + 1 < V ? goff[r + 1] : total) - o : 0u;
@@ -391,7 +402,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(
       recs[3 * v + 0] = make_float4(q[0], q[1], q[2], __uint_as_float(c));
       recs[3 * v + 1] = make_float4(q[3], q[4], q[5], q[6]);
       recs[3 * v + 2] = make_float4(q[7], q[8], 0.0f, 0.0f);
-      insert_lookup(v, vkeys[v], c, q, n_maps, vbase, slot_base, vmask, max_probe, vslots,
+      // the voxel's map (ranks and voxel ids of a map share its range
+      // [vbase[m], vbase[m + 1])): a CTA's ranks rarely span two maps
+      int m = seg_map[0];
+      while (m < seg_map[1] && (int64_t)vbase[m + 1] <= r) ++m;
+      insert_lookup(v, vkeys[v], c, q, m, slot_base, vmask, max_probe, vslots,
                     lslot_of, status);
     }
     __syncthreads();  // the stage is reused by the next batch
