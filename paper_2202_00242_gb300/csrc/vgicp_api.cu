@@ -109,8 +109,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
     return o;
   };
   const size_t o_point_off = take(sizeof(int64_t) * (n_maps + 1));
-  const int64_t n_blk32 = (n + 31) / 32;
-  const size_t o_blk_map = take(sizeof(uint32_t) * (size_t)std::max<int64_t>(n_blk32, 1));
   const size_t o_slot_base = take(sizeof(int64_t) * n_maps);
   const size_t o_vslot_base = take(sizeof(int64_t) * (n_maps + 1));
   const size_t o_cap_mask = take(sizeof(uint32_t) * n_maps);
@@ -151,7 +149,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   }
   char* b = static_cast<char*>(s->d_block);
   s->d_point_off = reinterpret_cast<int64_t*>(b + o_point_off);
-  s->d_blk_map = reinterpret_cast<uint32_t*>(b + o_blk_map);
   s->d_slot_base = reinterpret_cast<int64_t*>(b + o_slot_base);
   s->d_vslot_base = reinterpret_cast<int64_t*>(b + o_vslot_base);
   s->d_cap_mask = reinterpret_cast<uint32_t*>(b + o_cap_mask);
@@ -179,19 +176,9 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   cudaGetDevice(&s->device);
   std::vector<uint32_t> mask(n_maps);
   for (int32_t m = 0; m < n_maps; ++m) mask[m] = s->cap[m] - 1u;
-  // the map of the first point of every 32-point block (a warp of the build's
-  // per-point kernels starts its map search there)
-  std::vector<uint32_t> blk_map((size_t)std::max<int64_t>(n_blk32, 1), 0u);
-  for (int32_t m = 0, k = 0; k < n_blk32; ++k) {
-    while (m + 1 < n_maps && offsets[m + 1] <= 32 * (int64_t)k) ++m;
-    blk_map[(size_t)k] = (uint32_t)m;
-  }
   // metadata is small: synchronous copies keep the host vectors' lifetime simple
   e = cudaMemcpy(s->d_point_off, s->point_off.data(), sizeof(int64_t) * (n_maps + 1),
                  cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(s->d_blk_map, blk_map.data(), sizeof(uint32_t) * blk_map.size(),
-                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(s->d_slot_base, s->slot_base.data(), sizeof(int64_t) * n_maps,
                    cudaMemcpyHostToDevice);

@@ -42,6 +42,29 @@ namespace {
 
 constexpr int kThreads = 256;
 
+__device__ __forceinline__ int find_map(const int64_t* __restrict__ off, int32_t n_maps,
+                                        int64_t i) {
+  // last m with off[m] <= i (empty maps are skipped)
+  int lo = 0, hi = n_maps;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// find_map for the points of one warp, which are consecutive: the first active
+// lane searches, the others walk forward from its map (a warp spans few maps).
+__device__ __forceinline__ int find_map_warp(const int64_t* __restrict__ off, int32_t n_maps,
+                                             int64_t i) {
+  const unsigned am = __activemask();
+  const int leader = __ffs(am) - 1;
+  int m = ((int)(threadIdx.x & 31) == leader) ? find_map(off, n_maps, i) : 0;
+  m = __shfl_sync(am, m, leader);
+  while (m + 1 < n_maps && __ldg(off + m + 1) <= i) ++m;
+  return m;
+}
+
 __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
   atomicCAS(status, 0, code);
 }
@@ -58,17 +81,14 @@ __global__ void init_slots_kernel(Slot* __restrict__ slots, int64_t cap_total) {
 }
 
 __global__ void insert_kernel(const float* __restrict__ pts, int64_t n_total,
-                              const int64_t* __restrict__ point_off,
-                              const uint32_t* __restrict__ blk_map, int32_t n_maps,
+                              const int64_t* __restrict__ point_off, int32_t n_maps,
                               const int64_t* __restrict__ slot_base,
                               const uint32_t* __restrict__ cap_mask, float inv_r, double r,
                               int32_t max_probe, Slot* slots, uint32_t* __restrict__ pt_slot,
                               int32_t* status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    // the map of point i: from the map of its 32-point block, walking forward
-    int m = (int)__ldg(blk_map + (i >> 5));
-    while (m + 1 < n_maps && __ldg(point_off + m + 1) <= i) ++m;
+    const int m = find_map_warp(point_off, n_maps, i);
     const int kx = axis_key_target(__ldg(pts + 3 * i + 0), inv_r, r);
     const int ky = axis_key_target(__ldg(pts + 3 * i + 1), inv_r, r);
     const int kz = axis_key_target(__ldg(pts + 3 * i + 2), inv_r, r);
@@ -834,8 +854,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   const float inv_r = (float)(1.0 / s->resolution);
   const int g = grid_for(n, kThreads);
   uint32_t* first = s->d_vfill;  // reused: dead after the first scan, then zeroed
-  insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->d_blk_map, s->n_maps,
-                                        s->d_slot_base,
+  insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->n_maps, s->d_slot_base,
                                         s->d_cap_mask, inv_r, s->resolution, s->max_probe,
                                         s->d_slots, s->d_pt_slot, s->d_status);
   // voxel ids in order of first appearance (scan of the first flags), assigned

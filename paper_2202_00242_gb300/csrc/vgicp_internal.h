@@ -45,7 +45,6 @@ struct MapSet {
   int64_t vcap_total = 0;          //   counts of the first build (empty before it)
   // device: per-map metadata
   int64_t* d_point_off = nullptr;  // n_maps + 1
-  uint32_t* d_blk_map = nullptr;   // ceil(n_total / 32): map of point 32 k (per-warp start)
   int64_t* d_slot_base = nullptr;  // n_maps
   int64_t* d_vslot_base = nullptr; // n_maps + 1
   uint32_t* d_cap_mask = nullptr;  // n_maps
