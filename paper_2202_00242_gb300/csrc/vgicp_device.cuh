@@ -47,7 +47,7 @@ constexpr int kRecordF4 = 3;
 // device after the voxels are counted) inside a region sized for the worst case
 // V = n.  The low load factor (<= 1 / kLookupLoad) keeps most keys at home.
 #ifndef VGICP_LOOKUP_LOAD
-#define VGICP_LOOKUP_LOAD 8
+#define VGICP_LOOKUP_LOAD 16
 #endif
 constexpr uint32_t kLookupLoad = VGICP_LOOKUP_LOAD;
 struct __align__(64) VSlot {
