@@ -200,7 +200,7 @@ void release_set(MapSet* s) {
   if (--s->refcount == 0) free_set(s);
 }
 
-int sm_count_cache[64] = {0};
+int sm_count_cache[kMaxDevices] = {0};
 std::mutex sm_mutex;
 std::atomic<int64_t> g_launches{0};
 
@@ -245,7 +245,7 @@ void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed);
 int device_sm_count() {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
+  if (dev < 0 || dev >= kMaxDevices) dev = 0;
   std::lock_guard<std::mutex> g(sm_mutex);
   if (sm_count_cache[dev] == 0) {
     int n = 0;
