@@ -105,7 +105,7 @@ typedef struct {
  * read during the call's kernels only; symmetric positive semi-definite, as the
  * regularised k-nearest-neighbour covariances are).  resolution > 0.  n >= 0 (an empty map
  * is valid).  *out receives a new handle.  The call synchronizes the stream once,
- * after counting the voxels, to size the lookup table (next pow2 >= max(8 V,
+ * after counting the voxels, to size the lookup table (next pow2 >= max(16 V,
  * 2 n) slots of 64 B); the rest is asynchronous: check vgicp_voxelmap_status()
  * before relying on the contents. */
 int vgicp_build_voxelmap(const float* points, const float* covs, int64_t n, double resolution,
@@ -148,6 +148,14 @@ int vgicp_voxelmap_info(const vgicp_map* map, vgicp_stream_t stream, int64_t* nu
  * means V x 3 and covs V x 6 (float32).  Any output may be NULL. */
 int vgicp_voxelmap_export(const vgicp_map* map, vgicp_stream_t stream, int64_t max_voxels,
                           int64_t* keys, int32_t* counts, float* means, float* covs);
+
+/* Copies the map's voxel-grouped cloud (the cloud a map-as-source factor reads,
+ * Sec. III-F): its n rows with the points of each voxel contiguous and in
+ * ascending input index, the voxels in Morton order within chunks of the map's
+ * voxels.  points: device n x 3, covs: device n x 6 (either may be NULL);
+ * asynchronous on stream. */
+int vgicp_voxelmap_grouped_cloud(const vgicp_map* map, vgicp_stream_t stream, float* points,
+                                 float* covs);
 
 /* ------------------------------------------------------------------------ */
 /* Linearization (Eqs. 2-3 and the Hessian factor of Sec. III-A).             */

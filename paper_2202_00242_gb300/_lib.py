@@ -45,6 +45,7 @@ SIGNATURES = {
     "vgicp_voxelmap_status": (ctypes.c_int, [P, P]),
     "vgicp_voxelmap_info": (ctypes.c_int, [P, P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "vgicp_voxelmap_export": (ctypes.c_int, [P, P, i64, P, P, P, P]),
+    "vgicp_voxelmap_grouped_cloud": (ctypes.c_int, [P, P, P, P]),
     "vgicp_linearize": (ctypes.c_int, [P, P, P, i64, P, P, P, ctypes.POINTER(LinOpts), P]),
     "vgicp_linearize_noalloc": (ctypes.c_int, [P, P, P, i64, P, P, P, ctypes.POINTER(LinOpts),
                                                P]),

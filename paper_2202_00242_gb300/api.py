@@ -105,6 +105,15 @@ class VoxelMap:
             covs.ctypes.data_as(ctypes.c_void_p)))
         return {"keys": keys[:V], "counts": counts[:V], "means": means[:V], "covs": covs[:V]}
 
+    def grouped_cloud(self, stream=None):
+        """The map's voxel-grouped cloud (points n x 3, covs n x 6, on the device)."""
+        pts = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+        cov = torch.empty((self.n, 6), dtype=torch.float32, device="cuda")
+        check(_lib.load().vgicp_voxelmap_grouped_cloud(
+            self._h, _stream_ptr(stream), ctypes.c_void_p(pts.data_ptr()),
+            ctypes.c_void_p(cov.data_ptr())))
+        return pts, cov
+
     def close(self):
         if self._h is not None and self._h.value:
             _lib.load().vgicp_destroy_voxelmap(self._h)

@@ -360,6 +360,22 @@ int vgicp_voxelmap_info(const vgicp_map* map, vgicp_stream_t stream, int64_t* nu
   return VGICP_OK;
 }
 
+int vgicp_voxelmap_grouped_cloud(const vgicp_map* map, vgicp_stream_t stream, float* points,
+                                 float* covs) {
+  g_error.clear();
+  if (!map) return set_error(VGICP_ERR_INVALID_ARG, "map is null");
+  const MapSet* s = map->set;
+  const int64_t a = s->point_off[map->index], b = s->point_off[map->index + 1];
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (b > a && points)
+    VGICP_CUDA_TRY(cudaMemcpyAsync(points, s->d_gpts + 3 * a, sizeof(float) * 3 * (b - a),
+                                   cudaMemcpyDeviceToDevice, st));
+  if (b > a && covs)
+    VGICP_CUDA_TRY(cudaMemcpyAsync(covs, s->d_gcovs + 6 * a, sizeof(float) * 6 * (b - a),
+                                   cudaMemcpyDeviceToDevice, st));
+  return VGICP_OK;
+}
+
 int vgicp_voxelmap_export(const vgicp_map* map, vgicp_stream_t stream, int64_t max_voxels,
                           int64_t* keys, int32_t* counts, float* means, float* covs) {
   int64_t V = 0;
