@@ -151,6 +151,35 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
   return -1;
 }
 
+// One of the 27 neighbour probes: the lookup, reading a slot's second 32 B (the
+// Cholesky factor) only when its key matches (most neighbours are empty, and
+// their probe then reads one 32-B sector).
+__device__ __forceinline__ int lookup_neighbour(const MapDesc& md, uint32_t mask, int kx, int ky,
+                                               int kz, uint64_t pol, float4& r0, float4& r1,
+                                               float4& r2) {
+  if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) return -1;
+  const unsigned long long key = pack_key(kx, ky, kz);
+  uint32_t h = hash_key(kx, ky, kz) & mask;
+  for (int p = 0; p < md.max_probe; ++p) {
+    uint32_t a[8];
+    const VSlot* t = md.vslots + h;
+    ld_v8(t, pol, a);
+    const unsigned long long k = slot_key(a);
+    if (k == key) {
+      uint32_t b[8];
+      ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
+      r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
+      r1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
+                       __uint_as_float(b[3]));
+      r2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
+      return (int)a[2];
+    }
+    if (k == kEmptyKey || (p == 0 && a[7] == 0u)) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
 // Accumulator layout (float):
 //   0..5   H_ww (00 01 02 11 12 22)      6..14 H_wv (row-major, w rows, v cols)
 //   15..20 H_vv (00 01 02 11 12 22)      21..23 b_w   24..26 b_v   27 err
@@ -881,7 +910,8 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
             float4 a0, a1, a2;
-            const int vid = lookup(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
+            const int vid =
+                lookup_neighbour(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
             if (vid < 0) continue;
             term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
           }
