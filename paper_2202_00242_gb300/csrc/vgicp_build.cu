@@ -9,11 +9,11 @@
 //             build table is left empty by the scatter)
 //   insert    per point: exact key, open-addressing insert (CAS on the 64-bit
 //             key, bounded linear probe), count, smallest point index
-//   scan      first flags (1 if a point is the smallest index of its voxel),
-//             voxel id = number of first points before it (so voxels are
-//             numbered in order of first appearance, map by map); its last
-//             pass gives each first point's voxel its count, key and, in the
-//             slot, its id
+//   number    first points (the smallest index of their voxel) marked in a
+//             bitmap; voxel id = number of first points before the voxel's
+//             (a scan of the words' popcounts), so voxels are numbered in order
+//             of first appearance, map by map; each first point gives its voxel
+//             its count, key and, in the slot, its id
 //   sort      per map chunk: the voxels in Morton order of their keys (rank)
 //   scan      offsets of the voxels' point lists, in rank order and by voxel
 //   scatter   per point: append its index to its voxel's list; the voxel's
@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -141,14 +142,6 @@ __global__ void reset_tables_kernel(int64_t n_max, const uint32_t* __restrict__ 
   }
 }
 
-__global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __restrict__ point_off,
-                             const uint32_t* __restrict__ vid, const uint32_t* __restrict__ n_vox,
-                             uint32_t* __restrict__ vbase) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m > n_maps) return;
-  int64_t o = point_off[m];
-  vbase[m] = (o < n_total) ? vid[o] : *n_vox;
-}
 
 
 // Per point: append its index to its voxel's list.  The voxel's last point
@@ -157,15 +150,15 @@ __global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __r
 // slot, whose sector it has just read: the build table is empty again when the
 // scatter ends, ready for the next build.
 __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot, Slot* slots,
-                               const uint32_t* __restrict__ base,
-                               const uint32_t* __restrict__ vcount, uint32_t* vfill,
+                               const uint32_t* __restrict__ base, uint32_t* vfill,
                                uint32_t* __restrict__ plist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = pt_slot[i];
     if (s == kNoSlot) continue;
-    const uint32_t v = slots[s].vid;
-    const uint32_t c = vcount[v];
+    // one read of the slot: voxel id and count
+    const uint4 w = *reinterpret_cast<const uint4*>(slots + s);
+    const uint32_t v = w.z, c = w.w;
     const uint32_t f = atomicAdd(vfill + v, 1u);
     plist[base[v] + f] = (uint32_t)i;
     if (f + 1u == c) {
@@ -431,8 +424,8 @@ __device__ __forceinline__ uint32_t morton_of_key(unsigned long long key) {
 }
 
 // One CTA per (map, chunk): bitonic sort of the chunk's voxels by Morton code in
-// shared memory (ties by voxel id); vrank[v] = position of voxel v in that order,
-// vorder[rank] = v and gcount[rank] = the voxel's point count.
+// shared memory (ties by voxel id); vorder[rank] = v and gcount[rank] = the
+// voxel's point count.
 //
 // Element i lives at i + i / 16 (one pad word per 16), which keeps every access
 // pattern below free of bank conflicts.  Each pass loads a group of up to 16
@@ -478,7 +471,7 @@ __device__ __forceinline__ void bitonic_pass(unsigned long long* sk, uint32_t N,
 __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
     const int2* __restrict__ chunks, const uint32_t* __restrict__ vbase,
     const unsigned long long* __restrict__ vkeys, const uint32_t* __restrict__ vcount,
-    uint32_t* __restrict__ vrank, uint32_t* __restrict__ vorder, uint32_t* __restrict__ gcount) {
+    uint32_t* __restrict__ vorder, uint32_t* __restrict__ gcount) {
   extern __shared__ unsigned long long sk[];
   const int m = chunks[blockIdx.x].x;
   const uint32_t V = vbase[m + 1] - vbase[m];
@@ -487,7 +480,6 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
   const uint32_t cnt = min((uint32_t)kMortonChunk, V - lo);
 #ifdef VGICP_NO_MORTON
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    vrank[vbase[m] + lo + i] = vbase[m] + lo + i;
     vorder[vbase[m] + lo + i] = vbase[m] + lo + i;
     gcount[vbase[m] + lo + i] = vcount[vbase[m] + lo + i];
   }
@@ -537,7 +529,6 @@ __global__ void __launch_bounds__(kSortThreads) morton_sort_kernel(
   }
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const uint32_t v = first + (uint32_t)(sk[sort_phys(i)] & 0xFFFFFFFFull);
-    vrank[v] = first + i;
     vorder[first + i] = v;
     gcount[first + i] = vcount[v];
   }
@@ -629,28 +620,6 @@ __global__ void scan_tile_sums_kernel(const uint32_t* __restrict__ in, int64_t n
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// First pass of the first-appearance scan: first[i] = 1 if point i is the
-// smallest index of its voxel (the build-table slot holds that index), and the
-// tile sums of these flags.
-__global__ void first_sums_kernel(const uint32_t* __restrict__ pt_slot,
-                                  const Slot* __restrict__ slots, int64_t n,
-                                  uint32_t* __restrict__ first, uint32_t* __restrict__ sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
-  uint32_t ps[kScanPerThread];
-#pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) ps[k] = (base + k < n) ? pt_slot[base + k] : kNoSlot;
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) {
-    const uint32_t f = (ps[k] != kNoSlot && slots[ps[k]].vid == (uint32_t)(base + k)) ? 1u : 0u;
-    if (base + k < n) first[base + k] = f;
-    s += f;
-  }
-  __shared__ uint32_t total;
-  block_exclusive<kScanThreads>(s, &total);
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
-}
-
 // One CTA: each thread scans a contiguous run of the tile sums.
 constexpr int kScanSumsThreads = 1024;
 __global__ void __launch_bounds__(kScanSumsThreads) scan_sums_kernel(
@@ -689,40 +658,6 @@ __global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_m
   }
 }
 
-// Third pass of the first-appearance scan fused with the voxel assignment:
-// ids[i] = number of first points before point i, and each first point (the
-// smallest index of its voxel) gives its voxel that id: the voxel's count and
-// key are recorded by id and the id replaces the index in the build-table slot.
-__global__ void scan_assign_kernel(const uint32_t* __restrict__ first, uint32_t* __restrict__ ids,
-                                   int64_t n, const uint32_t* __restrict__ sums,
-                                   const uint32_t* __restrict__ pt_slot, Slot* slots,
-                                   uint32_t* __restrict__ vcount,
-                                   unsigned long long* __restrict__ vkeys) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
-  uint32_t f[kScanPerThread];
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) {
-    f[k] = (base + k < n) ? first[base + k] : 0u;
-    s += f[k];
-  }
-  __shared__ uint32_t total;
-  uint32_t run = block_exclusive<kScanThreads>(s, &total) + sums[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) {
-    if (base + k < n) {
-      ids[base + k] = run;
-      if (f[k]) {
-        Slot* sl = slots + pt_slot[base + k];
-        vcount[run] = sl->count;
-        vkeys[run] = sl->key;
-        sl->vid = run;
-      }
-    }
-    run += f[k];
-  }
-}
-
 // Last pass of the scan of the rank-ordered counts: goff[r] = the offset of rank
 // r's list, also stored by voxel (base[vorder[r]]) for the scatter.
 __global__ void scan_lists_kernel(const uint32_t* __restrict__ gcount, uint32_t* __restrict__ goff,
@@ -748,6 +683,74 @@ __global__ void scan_lists_kernel(const uint32_t* __restrict__ gcount, uint32_t*
     }
     run += v[k];
   }
+}
+
+// ---- first-appearance numbering -----------------------------------------
+// A point is its voxel's first if its index is the smallest of the voxel (the
+// build-table slot holds that index after the insert).  The first points are
+// marked in a bitmap (one warp ballot per 32 points); a voxel's id is the number
+// of marked points before its first point (an exclusive scan of the words'
+// popcounts), so voxels are numbered in order of first appearance, map by map.
+
+// One thread per point; every warp is whole (the grid covers n rounded up to
+// 32), so the ballot sees all 32 lanes.
+__global__ void first_bits_kernel(const uint32_t* __restrict__ pt_slot,
+                                  const Slot* __restrict__ slots, int64_t n,
+                                  uint32_t* __restrict__ bitmap) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool f = false;
+  if (i < n) {
+    const uint32_t ps = pt_slot[i];
+    f = ps != kNoSlot && slots[ps].vid == (uint32_t)i;
+  }
+  const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
+  if ((threadIdx.x & 31) == 0 && i < n) bitmap[i >> 5] = b;
+}
+
+__global__ void popc_words_kernel(const uint32_t* __restrict__ bitmap, int64_t n_words,
+                                  uint32_t* __restrict__ out) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    out[w] = (uint32_t)__popc(bitmap[w]);
+}
+
+// Number of first points before point i (wscan: the exclusive scan of the words'
+// popcounts; the word of index n exists and has no bit at or above n).
+__device__ __forceinline__ uint32_t first_rank(const uint32_t* __restrict__ bitmap,
+                                               const uint32_t* __restrict__ wscan, uint32_t i) {
+  const uint32_t w = i >> 5;
+  return wscan[w] + (uint32_t)__popc(bitmap[w] & ((1u << (i & 31u)) - 1u));
+}
+
+// Each first point gives its voxel its id: the voxel's count and key are
+// recorded by id and the id replaces the index in the build-table slot.
+__global__ void assign_ids_kernel(const uint32_t* __restrict__ bitmap,
+                                  const uint32_t* __restrict__ wscan, int64_t n,
+                                  const uint32_t* __restrict__ pt_slot, Slot* slots,
+                                  uint32_t* __restrict__ vcount,
+                                  unsigned long long* __restrict__ vkeys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!((bitmap[i >> 5] >> (i & 31)) & 1u)) continue;
+    const uint32_t id = first_rank(bitmap, wscan, (uint32_t)i);
+    Slot* sl = slots + pt_slot[i];
+    vcount[id] = sl->count;
+    vkeys[id] = sl->key;
+    sl->vid = id;
+  }
+}
+
+// vbase[m] = voxels of the maps before m; vbase[n_maps] and *n_vox = all.
+__global__ void vbase_kernel(int32_t n_maps, int64_t n_total, const int64_t* __restrict__ point_off,
+                             const uint32_t* __restrict__ bitmap,
+                             const uint32_t* __restrict__ wscan, uint32_t* __restrict__ vbase,
+                             uint32_t* __restrict__ n_vox) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > n_maps) return;
+  const int64_t o = m < n_maps ? point_off[m] : n_total;
+  const uint32_t v = first_rank(bitmap, wscan, (uint32_t)o);
+  vbase[m] = v;
+  if (m == n_maps) *n_vox = v;
 }
 
 // One thread per element (no grid-stride cap): CTAs are dispatched roughly in
@@ -853,47 +856,57 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   }
   const float inv_r = (float)(1.0 / s->resolution);
   const int g = grid_for(n, kThreads);
-  uint32_t* first = s->d_vfill;  // reused: dead after the first scan, then zeroed
   insert_kernel<<<g, kThreads, 0, st>>>(points, n, s->d_point_off, s->n_maps, s->d_slot_base,
                                         s->d_cap_mask, inv_r, s->resolution, s->max_probe,
                                         s->d_slots, s->d_pt_slot, s->d_status);
-  // voxel ids in order of first appearance (scan of the first flags), assigned
-  // to the voxels in the scan's last pass
+  // voxel ids in order of first appearance: first points marked in d_flag, the
+  // words' popcounts scanned in d_vfill (both dead afterwards)
   int rc = VGICP_OK;
   {
-    const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    first_sums_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(s->d_pt_slot, s->d_slots, n, first,
-                                                             s->d_scan_tmp);
-    scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(s->d_scan_tmp, nb, s->d_num_voxels);
-    scan_assign_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(
-        first, s->d_flag, n, s->d_scan_tmp, s->d_pt_slot, s->d_slots, s->d_vcount, s->d_vkeys);
+    const int64_t n_words = n / 32 + 1;
+    uint32_t* bitmap = s->d_flag;
+    uint32_t* wscan = s->d_vfill;
+    VGICP_CUDA_TRY(cudaMemsetAsync(bitmap + n / 32, 0, sizeof(uint32_t), st));
+    first_bits_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(s->d_pt_slot, s->d_slots, n,
+                                                                  bitmap);
+    popc_words_kernel<<<grid_for(n_words, kThreads), kThreads, 0, st>>>(bitmap, n_words, wscan);
+    rc = launch_exclusive_scan(wscan, wscan, n_words, nullptr, s->d_scan_tmp, nullptr, st);
+    if (rc != VGICP_OK) return rc;
+    assign_ids_kernel<<<g, kThreads, 0, st>>>(bitmap, wscan, n, s->d_pt_slot, s->d_slots,
+                                              s->d_vcount, s->d_vkeys);
+    vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
+                                                              bitmap, wscan, s->d_vbase,
+                                                              s->d_num_voxels);
     VGICP_CUDA_TRY(cudaGetLastError());
-    count_launches(3);
+    count_launches(4);
   }
-  vbase_kernel<<<(s->n_maps + 1 + 127) / 128, 128, 0, st>>>(s->n_maps, n, s->d_point_off,
-                                                            s->d_flag, s->d_num_voxels,
-                                                            s->d_vbase);
   if (!s->d_vblock) {
     rc = size_lookup_tables(s, st);
     if (rc != VGICP_OK) return rc;
   }
   // Morton order of the voxels (chunks of a map), the list offsets in that order,
   // the lists, then the per-voxel sums (which also write the grouped clouds).
-  // d_flag (voxel id per first point) is dead after vbase, d_vfill (first flags)
-  // after the first scan.
-  uint32_t* vrank = s->d_flag;
+  // d_vfill (first flags) is dead after the first scan.
   uint32_t* vorder = s->d_voff;
   uint32_t* gcount = s->d_vfill;
-  static bool sort_attr = false;
-  if (!sort_attr) {
-    VGICP_CUDA_TRY(cudaFuncSetAttribute(morton_sort_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(unsigned long long) * kSortSmemElems)));
-    sort_attr = true;
+  {
+    // the sort's shared memory is above the default limit: opt in once per device
+    static std::mutex attr_mu;
+    static bool attr_set[kMaxDevices] = {false};
+    int dev = 0;
+    VGICP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+      return set_error(VGICP_ERR_INVALID_ARG, "device index beyond the supported range");
+    std::lock_guard<std::mutex> lock(attr_mu);
+    if (!attr_set[dev]) {
+      VGICP_CUDA_TRY(cudaFuncSetAttribute(morton_sort_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(unsigned long long) * kSortSmemElems)));
+      attr_set[dev] = true;
+    }
   }
   morton_sort_kernel<<<s->n_chunks, kSortThreads, sizeof(unsigned long long) * kSortSmemElems,
-                       st>>>(
-      s->d_chunks, s->d_vbase, s->d_vkeys, s->d_vcount, vrank, vorder, gcount);
+                       st>>>(s->d_chunks, s->d_vbase, s->d_vkeys, s->d_vcount, vorder, gcount);
   VGICP_CUDA_TRY(cudaGetLastError());
   // list offsets in rank order, and by voxel
   {
@@ -909,7 +922,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   }
   VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
   scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of,
-                                         s->d_vcount, s->d_vfill, s->d_plist);
+                                         s->d_vfill, s->d_plist);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
     max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);
@@ -925,9 +938,9 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
       s->d_gpts, s->d_gcovs, s->d_vkeys, s->n_maps, s->d_vbase, s->d_vslot_base, s->d_vmask,
       s->max_probe, s->d_vslots, s->d_lslot_of, s->d_status);
   VGICP_CUDA_TRY(cudaGetLastError());
-  // insert, vbase, sort, scatter, vslot init, finalize (+ reset or init: 1; the two
-  // scans: 3 each)
-  count_launches(6);
+  // insert, sort, scatter, vslot init, finalize (+ reset or init: 1; numbering: 4;
+  // the two scans: 3 each)
+  count_launches(5);
   s->built = true;
   return VGICP_OK;
 }

@@ -59,7 +59,7 @@ struct MapSet {
   int32_t* d_status = nullptr;              // 1
   // device: build scratch (kept for rebuilds)
   uint32_t* d_pt_slot = nullptr;  // n_total: build-table slot of each point
-  uint32_t* d_flag = nullptr;     // n_total: voxel id of first points, then rank of each voxel
+  uint32_t* d_flag = nullptr;     // n_total: voxel id of each point (read at map starts)
   uint32_t* d_vcount = nullptr;   // n_total: points per voxel
   uint32_t* d_voff = nullptr;     // n_total: voxel at each rank
   uint32_t* d_vfill = nullptr;    // n_total: first-point flags, counts by rank, list fill
