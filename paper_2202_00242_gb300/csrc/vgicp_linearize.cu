@@ -151,35 +151,6 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
   return -1;
 }
 
-// One of the 27 neighbour probes: the lookup, reading a slot's second 32 B (the
-// Cholesky factor) only when its key matches (most neighbours are empty, and
-// their probe then reads one 32-B sector).
-__device__ __forceinline__ int lookup_neighbour(const MapDesc& md, uint32_t mask, int kx, int ky,
-                                               int kz, uint64_t pol, float4& r0, float4& r1,
-                                               float4& r2) {
-  if (!key_in_range(kx) || !key_in_range(ky) || !key_in_range(kz)) return -1;
-  const unsigned long long key = pack_key(kx, ky, kz);
-  uint32_t h = hash_key(kx, ky, kz) & mask;
-  for (int p = 0; p < md.max_probe; ++p) {
-    uint32_t a[8];
-    const VSlot* t = md.vslots + h;
-    ld_v8(t, pol, a);
-    const unsigned long long k = slot_key(a);
-    if (k == key) {
-      uint32_t b[8];
-      ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
-      r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
-      r1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
-                       __uint_as_float(b[3]));
-      r2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
-      return (int)a[2];
-    }
-    if (k == kEmptyKey || (p == 0 && a[7] == 0u)) return -1;
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
-
 // Accumulator layout (float):
 //   0..5   H_ww (00 01 02 11 12 22)      6..14 H_wv (row-major, w rows, v cols)
 //   15..20 H_vv (00 01 02 11 12 22)      21..23 b_w   24..26 b_v   27 err
@@ -799,6 +770,8 @@ template <int NEIGH, int MODE, bool DBG>
 __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
     linearize_simple_kernel(const __grid_constant__ LinLaunch L) {
   __shared__ float red[kSimpleThreads / 32][kAcc];
+  // 27 neighbours: each thread's hits (slot offsets) of its current point
+  __shared__ uint32_t hits[NEIGH == 27 ? 27 * kSimpleThreads : 1];
   __shared__ ItemConst ic;
   __shared__ int next_item;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -906,15 +879,58 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
         const int own = lookup(md, mask, kx, ky, kz, pol, a0, a1, a2);
         L.corr_out[p] = own < 0 ? -1 : (int)((uint32_t)own - vbase);
       }
+      // the 27 probes first, hits recorded; then the terms, hit by hit, so a
+      // warp evaluates a term while most of its lanes still have one.  The
+      // probes go a row of three neighbours at a time, their home slots' first
+      // 32 B (key, spill flag) loaded together; a miss whose home slot holds
+      // another key with its spill flag set probes on
+      int nh = 0;
       for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            float4 a0, a1, a2;
-            const int vid =
-                lookup_neighbour(md, mask, kx + dx, ky + dy, kz + dz, pol, a0, a1, a2);
-            if (vid < 0) continue;
-            term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int yy = ky + dy, zz = kz + dz;
+          const bool row_ok = key_in_range(yy) && key_in_range(zz);
+          uint32_t A[3][8];
+          uint32_t hh[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            hh[j] = hash_key(kx + j - 1, yy, zz) & mask;
+            ld_v8(md.vslots + hh[j], pol, A[j]);
           }
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int xx = kx + j - 1;
+            if (!row_ok || !key_in_range(xx)) continue;
+            const unsigned long long key = pack_key(xx, yy, zz);
+            const unsigned long long k0 = slot_key(A[j]);
+            int hs = -1;
+            if (k0 == key) {
+              hs = (int)hh[j];
+            } else if (k0 != kEmptyKey && A[j][7] != 0u) {
+              uint32_t h = (hh[j] + 1) & mask;  // spilled keys: probe on
+              for (int q = 1; q < md.max_probe; ++q) {
+                uint32_t a[8];
+                ld_v8(md.vslots + h, pol, a);
+                const unsigned long long k = slot_key(a);
+                if (k == key) { hs = (int)h; break; }
+                if (k == kEmptyKey) break;
+                h = (h + 1) & mask;
+              }
+            }
+            if (hs >= 0) hits[27 * threadIdx.x + nh++] = (uint32_t)hs;
+          }
+        }
+      for (int k = 0; k < nh; ++k) {
+        const VSlot* t = md.vslots + hits[27 * threadIdx.x + k];
+        uint32_t a[8], b[8];
+        ld_v8(t, pol, a);
+        ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
+        const float4 a0 =
+            make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
+        const float4 a1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]),
+                                      __uint_as_float(b[2]), __uint_as_float(b[3]));
+        const float4 a2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
+        term<MODE>(acc, P, x, y, z, c, qx, qy, qz, a0, a1, a2);
+      }
     }
 
 #pragma unroll
