@@ -34,9 +34,11 @@ constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 //   r2 = (C'yz, C'zz, 0, 0)
 constexpr int kRecordF4 = 3;
 
-// Lookup table slot with the voxel Gaussian inline (64 B, 64-B aligned): one
-// probe is two independent 256-bit loads.
-//   bytes  0..31: key (u64), vid (u32), count (u32), mu' (3 x f32), spill (u32)
+// Lookup table slot with the voxel Gaussian inline (64 B, 64-B aligned): a
+// lookup is two independent 256-bit loads; a probe that needs only the key and
+// the spill flag reads the first 16 B.
+//   bytes  0..15: key (u64), spill (u32), vid (u32)
+//   bytes 16..31: count (u32), mu' (3 x f32)
 //   bytes 32..63: L, the Cholesky factor of C' (6 x f32: l00 l10 l20 l11 l21
 //                 l22), pad
 // Linear probing from the key's home slot h.  spill (of slot h) is nonzero iff
@@ -52,14 +54,16 @@ constexpr int kRecordF4 = 3;
 constexpr uint32_t kLookupLoad = VGICP_LOOKUP_LOAD;
 struct __align__(64) VSlot {
   unsigned long long key;
+  uint32_t spill;
   uint32_t vid;
   uint32_t count;
   float mu[3];
-  uint32_t spill;
   float cov[6];
   float pad1[2];
 };
 static_assert(sizeof(VSlot) == 64, "VSlot is 64 B");
+// 32-bit words of the first half as loaded: key 0..1, then these
+constexpr int kSlotSpill = 2, kSlotVid = 3, kSlotMu = 5;
 
 // Per-map descriptor read by the linearize kernels.
 struct MapDesc {

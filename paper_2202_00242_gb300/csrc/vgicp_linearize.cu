@@ -119,6 +119,12 @@ __device__ __forceinline__ void ld_v8(const void* p, uint64_t policy, uint32_t (
 __device__ __forceinline__ unsigned long long slot_key(const uint32_t (&a)[8]) {
   return (unsigned long long)a[0] | ((unsigned long long)a[1] << 32);
 }
+// A slot's first 16 B: key (words 0, 1), spill flag, vid.
+__device__ __forceinline__ void ld_v4(const void* p, uint64_t policy, uint32_t (&w)[4]) {
+  asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+      : "l"(p), "l"(policy));
+}
 __device__ __forceinline__ uint64_t policy_evict_last_l() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -139,13 +145,14 @@ __device__ __forceinline__ int lookup(const MapDesc& md, uint32_t mask, int kx, 
     ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
     const unsigned long long k = slot_key(a);
     if (k == key) {
-      r0 = make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
+      r0 = make_float4(__uint_as_float(a[kSlotMu]), __uint_as_float(a[kSlotMu + 1]),
+                       __uint_as_float(a[kSlotMu + 2]), 0.f);
       r1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
                        __uint_as_float(b[3]));
       r2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
-      return (int)a[2];
+      return (int)a[kSlotVid];
     }
-    if (k == kEmptyKey || (p == 0 && a[7] == 0u)) return -1;  // empty, or nothing spilled
+    if (k == kEmptyKey || (p == 0 && a[kSlotSpill] == 0u)) return -1;  // empty, or nothing spilled
     h = (h + 1) & mask;
   }
   return -1;
@@ -582,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
       if (live[k]) {
         unsigned long long t = slot_key(sa[k]);
         uint32_t hh = h[k];
-        for (int p = 1; t != key[k] && t != kEmptyKey && (p > 1 || sa[k][7] != 0u) &&
+        for (int p = 1; t != key[k] && t != kEmptyKey && (p > 1 || sa[k][kSlotSpill] != 0u) &&
                         p < md.max_probe;
              ++p) {
           hh = (hh + 1) & mask;
@@ -591,9 +598,9 @@ __global__ void __launch_bounds__(kThreads, VGICP_MIN_BLOCKS) linearize_tma_kern
           t = slot_key(sa[k]);
         }
         if (t == key[k]) {
-          vid[k] = (int)sa[k][2];
-          r0[k] = make_float4(__uint_as_float(sa[k][4]), __uint_as_float(sa[k][5]),
-                              __uint_as_float(sa[k][6]), 0.f);
+          vid[k] = (int)sa[k][kSlotVid];
+          r0[k] = make_float4(__uint_as_float(sa[k][kSlotMu]), __uint_as_float(sa[k][kSlotMu + 1]),
+                              __uint_as_float(sa[k][kSlotMu + 2]), 0.f);
           r1[k] = make_float4(__uint_as_float(sb[k][0]), __uint_as_float(sb[k][1]),
                               __uint_as_float(sb[k][2]), __uint_as_float(sb[k][3]));
           r2[k] = make_float4(__uint_as_float(sb[k][4]), __uint_as_float(sb[k][5]), 0.f, 0.f);
@@ -882,35 +889,37 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
       // the 27 probes first, hits recorded; then the terms, hit by hit, so a
       // warp evaluates a term while most of its lanes still have one.  The
       // probes go a row of three neighbours at a time, their home slots' first
-      // 32 B (key, spill flag) loaded together; a miss whose home slot holds
+      // 16 B (key, spill flag) loaded together; a miss whose home slot holds
       // another key with its spill flag set probes on
       int nh = 0;
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy) {
           const int yy = ky + dy, zz = kz + dz;
           const bool row_ok = key_in_range(yy) && key_in_range(zz);
-          uint32_t A[3][8];
+          uint32_t A[3][4];
           uint32_t hh[3];
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             hh[j] = hash_key(kx + j - 1, yy, zz) & mask;
-            ld_v8(md.vslots + hh[j], pol, A[j]);
+            ld_v4(md.vslots + hh[j], pol, A[j]);
           }
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             const int xx = kx + j - 1;
             if (!row_ok || !key_in_range(xx)) continue;
             const unsigned long long key = pack_key(xx, yy, zz);
-            const unsigned long long k0 = slot_key(A[j]);
+            const unsigned long long k0 =
+                (unsigned long long)A[j][0] | ((unsigned long long)A[j][1] << 32);
             int hs = -1;
             if (k0 == key) {
               hs = (int)hh[j];
-            } else if (k0 != kEmptyKey && A[j][7] != 0u) {
+            } else if (k0 != kEmptyKey && A[j][kSlotSpill] != 0u) {
               uint32_t h = (hh[j] + 1) & mask;  // spilled keys: probe on
               for (int q = 1; q < md.max_probe; ++q) {
-                uint32_t a[8];
-                ld_v8(md.vslots + h, pol, a);
-                const unsigned long long k = slot_key(a);
+                uint32_t a[4];
+                ld_v4(md.vslots + h, pol, a);
+                const unsigned long long k =
+                    (unsigned long long)a[0] | ((unsigned long long)a[1] << 32);
                 if (k == key) { hs = (int)h; break; }
                 if (k == kEmptyKey) break;
                 h = (h + 1) & mask;
@@ -924,8 +933,8 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
         uint32_t a[8], b[8];
         ld_v8(t, pol, a);
         ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
-        const float4 a0 =
-            make_float4(__uint_as_float(a[4]), __uint_as_float(a[5]), __uint_as_float(a[6]), 0.f);
+        const float4 a0 = make_float4(__uint_as_float(a[kSlotMu]), __uint_as_float(a[kSlotMu + 1]),
+                                      __uint_as_float(a[kSlotMu + 2]), 0.f);
         const float4 a1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]),
                                       __uint_as_float(b[2]), __uint_as_float(b[3]));
         const float4 a2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
