@@ -930,11 +930,12 @@ __global__ void __launch_bounds__(kSimpleThreads, VGICP_SIMPLE_MIN_BLOCKS)
         }
       for (int k = 0; k < nh; ++k) {
         const VSlot* t = md.vslots + hits[27 * threadIdx.x + k];
-        uint32_t a[8], b[8];
-        ld_v8(t, pol, a);
+        // count and mu' (bytes 16..31), then L (bytes 32..63)
+        uint32_t a[4], b[8];
+        ld_v4(reinterpret_cast<const char*>(t) + 16, pol, a);
         ld_v8(reinterpret_cast<const char*>(t) + 32, pol, b);
-        const float4 a0 = make_float4(__uint_as_float(a[kSlotMu]), __uint_as_float(a[kSlotMu + 1]),
-                                      __uint_as_float(a[kSlotMu + 2]), 0.f);
+        const float4 a0 = make_float4(__uint_as_float(a[1]), __uint_as_float(a[2]),
+                                      __uint_as_float(a[3]), 0.f);
         const float4 a1 = make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]),
                                       __uint_as_float(b[2]), __uint_as_float(b[3]));
         const float4 a2 = make_float4(__uint_as_float(b[4]), __uint_as_float(b[5]), 0.f, 0.f);
