@@ -126,7 +126,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   const size_t o_voff = take(sizeof(uint32_t) * n);
   const size_t o_vfill = take(sizeof(uint32_t) * n);
   const size_t o_plist = take(sizeof(uint32_t) * n);
-  const size_t o_vslot_of = take(sizeof(uint32_t) * n);
   const size_t o_lslot_of = take(sizeof(uint32_t) * n);
   std::vector<int2> chunks;
   for (int32_t m = 0; m < n_maps; ++m) {
@@ -166,7 +165,6 @@ int create_set(const int64_t* offsets, int32_t n_maps, double resolution,
   s->d_voff = reinterpret_cast<uint32_t*>(b + o_voff);
   s->d_vfill = reinterpret_cast<uint32_t*>(b + o_vfill);
   s->d_plist = reinterpret_cast<uint32_t*>(b + o_plist);
-  s->d_vslot_of = reinterpret_cast<uint32_t*>(b + o_vslot_of);
   s->d_lslot_of = reinterpret_cast<uint32_t*>(b + o_lslot_of);
   s->d_gpts = reinterpret_cast<float*>(b + o_gpts);
   s->d_goff = reinterpret_cast<uint32_t*>(b + o_goff);

@@ -150,8 +150,7 @@ __global__ void reset_tables_kernel(int64_t n_max, const uint32_t* __restrict__ 
 // slot, whose sector it has just read: the build table is empty again when the
 // scatter ends, ready for the next build.
 __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_slot, Slot* slots,
-                               const uint32_t* __restrict__ base, uint32_t* vfill,
-                               uint32_t* __restrict__ plist) {
+                               unsigned long long* bfill, uint32_t* __restrict__ plist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t s = pt_slot[i];
@@ -159,8 +158,10 @@ __global__ void scatter_kernel(int64_t n_total, const uint32_t* __restrict__ pt_
     // one read of the slot: voxel id and count
     const uint4 w = *reinterpret_cast<const uint4*>(slots + s);
     const uint32_t v = w.z, c = w.w;
-    const uint32_t f = atomicAdd(vfill + v, 1u);
-    plist[base[v] + f] = (uint32_t)i;
+    // (list base << 32 | fill): one atomic gives the point its place
+    const unsigned long long bf = atomicAdd(bfill + v, 1ull);
+    const uint32_t f = (uint32_t)bf;
+    plist[(uint32_t)(bf >> 32) + f] = (uint32_t)i;
     if (f + 1u == c) {
       Slot e;
       e.key = kEmptyKey;
@@ -659,11 +660,12 @@ __global__ void scan_tiles_kernel(const uint32_t* in, uint32_t* out, int64_t n_m
 }
 
 // Last pass of the scan of the rank-ordered counts: goff[r] = the offset of rank
-// r's list, also stored by voxel (base[vorder[r]]) for the scatter.
+// r's list, also stored by voxel for the scatter, as (base << 32 | fill 0).
 __global__ void scan_lists_kernel(const uint32_t* __restrict__ gcount, uint32_t* __restrict__ goff,
                                   int64_t n_max, const uint32_t* __restrict__ n_dev,
                                   const uint32_t* __restrict__ sums,
-                                  const uint32_t* __restrict__ vorder, uint32_t* __restrict__ base) {
+                                  const uint32_t* __restrict__ vorder,
+                                  unsigned long long* __restrict__ bfill) {
   const int64_t n = scan_len(n_max, n_dev);
   const int64_t b0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
   uint32_t v[kScanPerThread];
@@ -679,7 +681,7 @@ __global__ void scan_lists_kernel(const uint32_t* __restrict__ gcount, uint32_t*
   for (int k = 0; k < kScanPerThread; ++k) {
     if (b0 + k < n) {
       goff[b0 + k] = run;
-      base[vorder[b0 + k]] = run;
+      bfill[vorder[b0 + k]] = (unsigned long long)run << 32;  // fill 0
     }
     run += v[k];
   }
@@ -889,6 +891,9 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   // d_vfill (first flags) is dead after the first scan.
   uint32_t* vorder = s->d_voff;
   uint32_t* gcount = s->d_vfill;
+  // the lists' (base << 32 | fill) words, by voxel: in the record storage, which
+  // finalize fills only after the scatter (8 of its 48 B per voxel)
+  unsigned long long* bfill = reinterpret_cast<unsigned long long*>(s->d_recs);
   {
     // the sort's shared memory is above the default limit: opt in once per device
     static std::mutex attr_mu;
@@ -916,13 +921,11 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
     scan_sums_kernel<<<1, kScanSumsThreads, 0, st>>>(s->d_scan_tmp, nb, s->d_num_valid);
     scan_lists_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(gcount, s->d_goff, n,
                                                              s->d_num_voxels, s->d_scan_tmp,
-                                                             vorder, s->d_vslot_of);
+                                                             vorder, bfill);
     VGICP_CUDA_TRY(cudaGetLastError());
     count_launches(3);
   }
-  VGICP_CUDA_TRY(cudaMemsetAsync(s->d_vfill, 0, sizeof(uint32_t) * n, st));
-  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, s->d_vslot_of,
-                                         s->d_vfill, s->d_plist);
+  scatter_kernel<<<g, kThreads, 0, st>>>(n, s->d_pt_slot, s->d_slots, bfill, s->d_plist);
   int64_t max_cap = 16;
   for (int32_t m = 0; m < s->n_maps; ++m)
     max_cap = std::max<int64_t>(max_cap, s->vslot_base[m + 1] - s->vslot_base[m]);

@@ -64,7 +64,6 @@ struct MapSet {
   uint32_t* d_voff = nullptr;     // n_total: voxel at each rank
   uint32_t* d_vfill = nullptr;    // n_total: first-point flags, counts by rank, list fill
   uint32_t* d_plist = nullptr;    // n_total: point lists of the voxels, in rank order
-  uint32_t* d_vslot_of = nullptr; // n_total: list base of each voxel
   // kept from one build to the next: the lookup-table slot each voxel occupies,
   // so a rebuild empties just those (every other slot is empty already)
   uint32_t* d_lslot_of = nullptr; // n_total: lookup-table slot of each voxel (or kNoSlot)
