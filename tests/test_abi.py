@@ -55,6 +55,8 @@ def test_host_argument_checks_without_gpu(lib):
     rc = lib.vgicp_linearize(None, None, None, 0, None, None, None, None, None)
     assert rc == -1
     assert lib.vgicp_destroy_voxelmap(None) == 0
+    # a null map is refused before any copy
+    assert lib.vgicp_voxelmap_grouped_cloud(None, None, None, None) == -1
     opts = _lib.LinOpts(5, 0, 0, 0, None, None)
     rc = lib.vgicp_linearize_batched(None, 0, None, 0, None, 1, None, None, None,
                                      ctypes.byref(opts), None)
