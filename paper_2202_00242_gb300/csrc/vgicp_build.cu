@@ -888,7 +888,7 @@ int launch_build(MapSet* s, const float* points, const float* covs, cudaStream_t
   }
   // Morton order of the voxels (chunks of a map), the list offsets in that order,
   // the lists, then the per-voxel sums (which also write the grouped clouds).
-  // d_vfill (first flags) is dead after the first scan.
+  // d_vfill (the numbering's word scan) is dead after the id assignment.
   uint32_t* vorder = s->d_voff;
   uint32_t* gcount = s->d_vfill;
   // the lists' (base << 32 | fill) words, by voxel: in the record storage, which
